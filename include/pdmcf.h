@@ -1,0 +1,214 @@
+/*
+ * pdmcf.h — C ABI of the GB300 (sm_103a) PDMCF solver library (libpdmcf.so).
+ *
+ * Solves the all-pairs multicommodity network flow problem with destination-aggregated
+ * flows (Zhang & Boyd, "Solving Large Multicommodity Network Flow Problems on GPUs",
+ * Sec. 1.1, Eq. (e-prob)):
+ *
+ *     maximize   U(T) = sum_{i != j} u_ij(T_ij)
+ *     subject to F >= 0,  F^T 1 <= c,  T + F A^T = 0
+ *
+ * by the PDMCF method (Algorithm 2.1): PDHG with over-relaxation (Eq. e-pdhg-step) on the
+ * reduced Lagrangian (Eq. e-L), capped-simplex projection per edge (Sec. 2.3), entrywise
+ * utility proxes (Sec. 2.3), adaptive primal weight (Eq. e-primal_weight) and the step
+ * bound eta = 1/sqrt(2 d_max) (Eq. e-eta).
+ *
+ * Conventions (Sec. 1.1):
+ *   - nodes are 0..n-1, edge l goes from tail[l] to head[l]; the incidence matrix has
+ *     A[head[l], l] = +1, A[tail[l], l] = -1;
+ *   - T[i*n + j] (row-major) is the traffic from source j to destination i; the diagonal
+ *     holds T_ii = -sum_{j != i} T_ij, so T 1 = 0;
+ *   - F[i*m + l] (row-major) is the flow on edge l destined to node i;
+ *   - w[i*n + j] weights the utility of traffic j -> i; the diagonal is ignored.
+ *
+ * All functions return an int status (MCF_OK = 0 or a negative MCF_ERR_* code, or
+ * MCF_PENDING). On error, mcf_last_error() returns a message for the calling thread.
+ * Every function is safe to call from any thread; one problem handle must not be used by
+ * two calls at the same time (mcf_submit'ed work counts as a use until it completes).
+ * All solves run on the GPU; the library has no CPU fallback and fails with
+ * MCF_ERR_CUDA when no usable CUDA device is present.
+ */
+#ifndef PDMCF_H
+#define PDMCF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define MCF_OK                 0
+#define MCF_PENDING            1   /* mcf_poll: the ticket has not finished yet        */
+#define MCF_ERR_INVALID       -1   /* bad argument (sizes, ids, c <= 0, w <= 0, gamma) */
+#define MCF_ERR_NOT_CONNECTED -2   /* network is not strongly connected (Sec. 1.1)     */
+#define MCF_ERR_OOM           -3   /* device allocation failed                         */
+#define MCF_ERR_CUDA          -4   /* CUDA runtime error / no device                   */
+#define MCF_ERR_NUMERIC       -5   /* NaN or Inf in the iterates                       */
+#define MCF_ERR_NOT_CONVERGED -6   /* max_iters reached; results are still filled      */
+#define MCF_ERR_TIMEOUT       -7   /* mcf_wait timed out                               */
+#define MCF_ERR_BUSY          -8   /* submission queue full                            */
+#define MCF_ERR_OOM_BUDGET    -9   /* instance does not fit the serving HBM budget     */
+#define MCF_ERR_CANCELLED    -10   /* ticket cancelled before it completed             */
+
+/* ---------------------------------------------------------------- enums */
+#define MCF_LOG 0          /* u(s) = w log s                     (Sec. 1.1) */
+#define MCF_POW 1          /* u(s) = w s^gamma, gamma in (0, 1)  (Sec. 1.1) */
+
+#define MCF_FP32   0       /* float iterates, float storage of F                       */
+#define MCF_FP64   1       /* double iterates (small problems, exact parity checks)     */
+#define MCF_BF16_F 2       /* float iterates, bfloat16 storage of F, float accumulation */
+
+#define MCF_STOP_PAPER   0 /* stop when r^k < n m eps (Sec. 2.5, residual of Eq. e-res)   */
+#define MCF_STOP_REL_KKT 1 /* stop when the relative KKT measure (see mcf_result) < eps  */
+#define MCF_STOP_NONE    2 /* run exactly max_iters iterations                           */
+
+typedef struct mcf_problem mcf_problem;   /* opaque */
+typedef int64_t mcf_ticket;
+
+/* ---------------------------------------------------------------- options */
+typedef struct mcf_options {
+  double  eps;               /* tolerance for the stop test (default 1e-4)                 */
+  int     stop_mode;         /* MCF_STOP_* (default MCF_STOP_REL_KKT)                       */
+  int64_t max_iters;         /* iteration cap (default 100000)                              */
+  double  rho;               /* over-relaxation, Sec. 2.2 (default 1.9)                     */
+  double  theta;             /* primal weight smoothing, Eq. e-primal_weight (default 0.5)  */
+  int     k_adapt;           /* primal weight period, Sec. 2.4 (default 100)                */
+  double  tau;               /* primal weight threshold on Delta_F, Delta_Y (default 1e-5)  */
+  int64_t omega_freeze_iter; /* stop adapting omega from this iteration on; -1 = never      */
+  int     k_check;           /* stop test every k_check iterations (default 50)             */
+  int     precision;         /* MCF_FP32 | MCF_FP64 | MCF_BF16_F (default MCF_FP32)         */
+  int     warm_start;        /* 1: start from the problem's resident (F, Y, omega)          */
+  int     polish_iters;      /* MCF_BF16_F: extra FP32 iterations after convergence         */
+  int     use_graphs;        /* capture each k_check-iteration chunk in a CUDA graph (1)    */
+  int     device;            /* CUDA device ordinal (default 0)                             */
+  void*   cuda_stream;       /* cudaStream_t to run on; NULL = the library's own stream     */
+  double  omega0;            /* initial primal weight for cold starts (default 1.0)         */
+  int     shape;             /* kernel launch shape index (-1 = automatic); see
+                                mcf_shape_info. Lets tests and the tuner pick any shape
+                                whose capacity covers the problem                          */
+} mcf_options;
+
+/* ---------------------------------------------------------------- results */
+typedef struct mcf_result {
+  /* caller-owned output buffers (host memory), each optional (NULL = not wanted) */
+  double* T;           /* n*n, T[i*n+j]: traffic j -> i of the returned flow         */
+  double* F;           /* n*m, F[i*m+l]: the returned (projected) flow  F^{k-1/2}    */
+  double* Y;           /* n*n, Y[i*n+j]: the dual prox output Y^k                     */
+  /* scalars (always filled) */
+  int64_t iters;       /* PDHG iterations performed                                   */
+  int     status;      /* MCF_OK, MCF_ERR_NOT_CONVERGED, MCF_ERR_NUMERIC, ...         */
+  int     feasible;    /* 1 if every off-diagonal T_ij > 0 (Sec. 1.1 domain)          */
+  double  utility;     /* U(T), FP64 reduction (-inf if not feasible)                 */
+  double  dual_bound;  /* D(Y) >= U*: (-U)^*(Y) + sum_l c_l max(0, max_i (Y A)_il)     */
+  double  r;           /* residual r^k of Eq. (e-res) (inf if not feasible)            */
+  double  r_over_nm;   /* r / (n m), the paper's normalised residual                   */
+  double  rel_gap;     /* (D - U) / (1 + |U| + |D|)                                    */
+  double  rel_cons;    /* ||T(Y) - T||_F / (1 + ||T||_F), T(Y) = (u')^{-1}(-Y), off-diag */
+  double  rel_stat;    /* sqrt(r) / (1 + ||G||_F), G = U'A (Sec. 1.2)                  */
+  double  rel_kkt;     /* max(rel_gap, rel_cons, rel_stat)                             */
+  double  nonpos_frac; /* fraction of off-diagonal T_ij <= 0 (Sec. 3.1 diagnostic)      */
+  double  omega;       /* final primal weight                                          */
+  double  seconds;     /* wall time of the call                                        */
+} mcf_result;
+
+/* ---------------------------------------------------------------- problem lifecycle */
+
+/* Create a problem from the data of Eq. (e-prob) (Sec. 1.1).
+ *   n, m          node and edge counts (n >= 2, m >= 1)
+ *   tail, head    m edge endpoints, 0 <= id < n, tail != head, no duplicate pairs; the
+ *                 network must be strongly connected (Sec. 1.1), else MCF_ERR_NOT_CONNECTED
+ *   cap           m capacities c_l > 0
+ *   utility_kind  MCF_LOG or MCF_POW
+ *   w             n*n weights, w[i*n+j] > 0 for i != j (diagonal ignored)
+ *   gamma         MCF_POW only: NULL with gamma_len = 0 is invalid for MCF_POW; gamma_len
+ *                 = 1 (one exponent) or n*n (per pair, row-major like w); each in (0, 1)
+ *   out           receives the handle
+ * All arrays are host memory, copied; the caller keeps ownership. Device memory is
+ * allocated at the first solve, on the device named in its options. */
+int mcf_create_problem(int32_t n, int32_t m, const int32_t* tail, const int32_t* head,
+                       const double* cap, int utility_kind, const double* w,
+                       const double* gamma, int64_t gamma_len, mcf_problem** out);
+
+/* Replace the capacities (m values > 0). The resident iterate (F, Y, omega) is kept, so
+ * a following solve with warm_start = 1 re-solves from it (Sec. 3.1, warm start). */
+int mcf_update_capacities(mcf_problem* p, const double* cap);
+
+/* Replace the weights (n*n host values, > 0 off the diagonal); resident state kept. */
+int mcf_update_weights(mcf_problem* p, const double* w);
+
+/* Free the problem and its device memory. Must not be called while a ticket on it is
+ * pending. NULL is accepted. */
+int mcf_destroy_problem(mcf_problem* p);
+
+/* Size queries. */
+int mcf_problem_size(const mcf_problem* p, int32_t* n, int32_t* m);
+
+/* Device bytes one solve of this problem needs at the given precision. */
+int64_t mcf_problem_device_bytes(const mcf_problem* p, int precision);
+
+/* ---------------------------------------------------------------- solving */
+
+/* Fill *o with the paper's defaults (Sec. 2.2, 2.4, 2.5) and the library defaults above. */
+void mcf_options_default(mcf_options* o);
+
+/* Run Algorithm 2.1 on the GPU until the stop test passes or max_iters is reached
+ * (synchronous). Cold start: F^{-1/2} = 0, Y^0 = I - 1 1^T, omega^0 = omega0 (Sec. 2.5);
+ * warm_start = 1 continues from the problem's resident iterate. Fills *res (scalars and
+ * any non-NULL output buffers). Returns MCF_OK, MCF_ERR_NOT_CONVERGED (results filled),
+ * MCF_ERR_NUMERIC, MCF_ERR_OOM, MCF_ERR_CUDA or MCF_ERR_INVALID. */
+int mcf_solve(mcf_problem* p, const mcf_options* opts, mcf_result* res);
+
+/* Asynchronous solve: enqueue and return a ticket at once. The serving scheduler admits
+ * the request when its device footprint fits the HBM budget (mcf_serving_config) and
+ * advances it batched with the other resident requests. May return MCF_ERR_BUSY or
+ * MCF_ERR_OOM_BUDGET. The options are copied; the problem must stay alive until the
+ * ticket completes. */
+int mcf_submit(mcf_problem* p, const mcf_options* opts, mcf_ticket* ticket);
+
+/* Non-blocking: *status receives MCF_PENDING until the ticket finishes, then its final
+ * status, and *res (if not NULL) is filled as by mcf_solve. A finished ticket is released
+ * by the first poll that reports it. */
+int mcf_poll(mcf_ticket ticket, int* status, mcf_result* res);
+
+/* Blocking form of mcf_poll with a timeout in milliseconds (< 0: no limit). Returns
+ * MCF_ERR_TIMEOUT if the ticket is still pending when the limit passes. */
+int mcf_wait(mcf_ticket ticket, int64_t timeout_ms, int* status, mcf_result* res);
+
+/* Cancel a pending ticket; its poll then reports MCF_ERR_CANCELLED. */
+int mcf_cancel(mcf_ticket ticket);
+
+/* Serving configuration: HBM budget for admitted requests (bytes) and the maximum number
+ * of requests resident at once. Defaults: 120 GB, 256. */
+int mcf_serving_config(int64_t hbm_budget_bytes, int max_resident);
+
+/* Per-kernel device times of a timed solve (CUDA events recorded on the solve stream
+ * between consecutive kernels). Index 0 edge phase, 1 node phase, 2 residual check,
+ * 3 scalar tail. */
+typedef struct mcf_kernel_times {
+  double  ms[4];         /* summed device time per kernel kind                        */
+  int64_t launches[4];   /* launches per kernel kind                                  */
+  double  ms_total;      /* first to last event of the iteration launches             */
+} mcf_kernel_times;
+
+/* As mcf_solve, but launches every kernel individually (no CUDA graphs) with a CUDA event
+ * before and after it on the solve stream, and fills *kt. For measurement. */
+int mcf_solve_timed(mcf_problem* p, const mcf_options* opts, mcf_result* res,
+                    mcf_kernel_times* kt);
+
+/* Launch shape table: shape s gives `group` threads per edge/node, each holding `vpt`
+ * 16-byte chunks of the edge/node vector (capacity group*vpt chunks of 16 bytes of F).
+ * Returns the number of shapes; fills the three arrays (may be NULL) up to that count. */
+int mcf_shape_info(int* group, int* vpt, int* block);
+
+/* Message for the last error of the calling thread ("" if none). */
+const char* mcf_last_error(void);
+
+/* Library version string. */
+const char* mcf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDMCF_H */

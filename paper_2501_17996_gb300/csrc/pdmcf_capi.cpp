@@ -1,0 +1,287 @@
+// pdmcf_capi.cpp — the extern "C" boundary of libpdmcf.so (declared in include/pdmcf.h).
+//
+// Validates the problem data of Eq. (e-prob) (Zhang & Boyd, Sec. 1.1), builds the internal
+// edge order, and forwards solves to the CUDA driver (pdmcf_solver.cu) and the serving
+// scheduler (pdmcf_serve.cpp). No numerical work happens here.
+#include <stdint.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "pdmcf_internal.h"
+
+namespace pdmcf {
+
+int mcf_shape_count();
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+static int fail(int code, const std::string& msg) {
+  set_error(msg);
+  return code;
+}
+
+// Strong connectivity (Sec. 1.1: a directed path between every pair): every node is
+// reachable from node 0 along edges and along reversed edges.
+static bool strongly_connected(int n, const std::vector<int32_t>& tail,
+                               const std::vector<int32_t>& head) {
+  for (int dir = 0; dir < 2; ++dir) {
+    std::vector<std::vector<int32_t>> adj(n);
+    for (size_t l = 0; l < tail.size(); ++l) {
+      if (dir == 0) adj[tail[l]].push_back(head[l]);
+      else adj[head[l]].push_back(tail[l]);
+    }
+    std::vector<char> seen(n, 0);
+    std::vector<int32_t> stack{0};
+    seen[0] = 1;
+    int count = 1;
+    while (!stack.empty()) {
+      const int v = stack.back();
+      stack.pop_back();
+      for (int u : adj[v])
+        if (!seen[u]) { seen[u] = 1; ++count; stack.push_back(u); }
+    }
+    if (count != n) return false;
+  }
+  return true;
+}
+
+static void build_topology(int n, const std::vector<int32_t>& tail,
+                           const std::vector<int32_t>& head, Topology& t) {
+  const int m = (int)tail.size();
+  t.perm.resize(m);
+  std::iota(t.perm.begin(), t.perm.end(), 0);
+  std::stable_sort(t.perm.begin(), t.perm.end(),
+                   [&](int a, int b) { return head[a] < head[b]; });
+  t.e_tail.resize(m);
+  t.e_head.resize(m);
+  for (int e = 0; e < m; ++e) {
+    t.e_tail[e] = tail[t.perm[e]];
+    t.e_head[e] = head[t.perm[e]];
+  }
+  t.in_ptr.assign(n + 1, 0);
+  t.out_ptr.assign(n + 1, 0);
+  for (int e = 0; e < m; ++e) {
+    t.in_ptr[t.e_head[e] + 1]++;
+    t.out_ptr[t.e_tail[e] + 1]++;
+  }
+  for (int j = 0; j < n; ++j) {
+    t.in_ptr[j + 1] += t.in_ptr[j];
+    t.out_ptr[j + 1] += t.out_ptr[j];
+  }
+  t.out_idx.resize(m);
+  std::vector<int32_t> fill(t.out_ptr.begin(), t.out_ptr.end() - 1);
+  for (int e = 0; e < m; ++e) t.out_idx[fill[t.e_tail[e]]++] = e;
+  t.dmax = 0;
+  for (int j = 0; j < n; ++j) {
+    const int d = (t.in_ptr[j + 1] - t.in_ptr[j]) + (t.out_ptr[j + 1] - t.out_ptr[j]);
+    t.dmax = std::max(t.dmax, d);
+  }
+}
+
+static int check_weights(int n, const double* w) {
+  if (!w) return fail(MCF_ERR_INVALID, "w is NULL");
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      if (i == j) continue;
+      const double x = w[(size_t)i * n + j];
+      if (!(x > 0.0) || !std::isfinite(x))
+        return fail(MCF_ERR_INVALID, "weights must be finite and > 0 off the diagonal");
+    }
+  return MCF_OK;
+}
+
+static int check_caps(int m, const double* cap) {
+  if (!cap) return fail(MCF_ERR_INVALID, "cap is NULL");
+  for (int l = 0; l < m; ++l)
+    if (!(cap[l] > 0.0) || !std::isfinite(cap[l]))
+      return fail(MCF_ERR_INVALID, "capacities must be finite and > 0");
+  return MCF_OK;
+}
+
+int validate_options(const mcf_options* o) {
+  if (!o) return fail(MCF_ERR_INVALID, "options are NULL");
+  if (o->stop_mode != MCF_STOP_PAPER && o->stop_mode != MCF_STOP_REL_KKT &&
+      o->stop_mode != MCF_STOP_NONE)
+    return fail(MCF_ERR_INVALID, "unknown stop_mode");
+  if (o->stop_mode != MCF_STOP_NONE && !(o->eps > 0.0))
+    return fail(MCF_ERR_INVALID, "eps must be > 0");
+  if (o->max_iters < 1) return fail(MCF_ERR_INVALID, "max_iters must be >= 1");
+  if (!(o->rho > 0.0 && o->rho < 2.0)) return fail(MCF_ERR_INVALID, "rho must be in (0, 2)");
+  if (!(o->theta >= 0.0 && o->theta <= 1.0)) return fail(MCF_ERR_INVALID, "theta must be in [0, 1]");
+  if (o->k_adapt < 1) return fail(MCF_ERR_INVALID, "k_adapt must be >= 1");
+  if (o->k_check < 1) return fail(MCF_ERR_INVALID, "k_check must be >= 1");
+  if (o->precision != MCF_FP32 && o->precision != MCF_FP64 && o->precision != MCF_BF16_F)
+    return fail(MCF_ERR_INVALID, "unknown precision");
+  if (o->polish_iters < 0) return fail(MCF_ERR_INVALID, "polish_iters must be >= 0");
+  if (o->shape < -1 || o->shape >= mcf_shape_count()) return fail(MCF_ERR_INVALID, "unknown shape");
+  return MCF_OK;
+}
+
+}  // namespace pdmcf
+
+using namespace pdmcf;
+
+extern "C" {
+
+const char* mcf_last_error(void) { return g_last_error.c_str(); }
+
+const char* mcf_version(void) { return "pdmcf-gb300 0.1 (sm_103a)"; }
+
+void mcf_options_default(mcf_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->eps = 1e-4;
+  o->stop_mode = MCF_STOP_REL_KKT;
+  o->max_iters = 100000;
+  o->rho = 1.9;          // Sec. 2.2
+  o->theta = 0.5;        // Sec. 2.4
+  o->k_adapt = 100;      // Sec. 2.4
+  o->tau = 1e-5;         // Sec. 2.4, Algorithm 2.1 step 3
+  o->omega_freeze_iter = -1;
+  o->k_check = 50;
+  o->precision = MCF_FP32;
+  o->warm_start = 0;
+  o->polish_iters = 0;
+  o->use_graphs = 1;
+  o->device = 0;
+  o->cuda_stream = nullptr;
+  o->omega0 = 1.0;       // Sec. 2.5
+  o->shape = -1;
+}
+
+int mcf_create_problem(int32_t n, int32_t m, const int32_t* tail, const int32_t* head,
+                       const double* cap, int utility_kind, const double* w,
+                       const double* gamma, int64_t gamma_len, mcf_problem** out) {
+  if (!out) return fail(MCF_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (n < 2) return fail(MCF_ERR_INVALID, "n must be >= 2");
+  if (m < 1) return fail(MCF_ERR_INVALID, "m must be >= 1");
+  if (!tail || !head) return fail(MCF_ERR_INVALID, "tail/head are NULL");
+  if (utility_kind != MCF_LOG && utility_kind != MCF_POW)
+    return fail(MCF_ERR_INVALID, "utility_kind must be MCF_LOG or MCF_POW");
+  if ((int64_t)n * (int64_t)n > (int64_t)1 << 40) return fail(MCF_ERR_INVALID, "n too large");
+  std::vector<int32_t> t(tail, tail + m), h(head, head + m);
+  std::vector<int64_t> keys(m);
+  for (int l = 0; l < m; ++l) {
+    if (t[l] < 0 || t[l] >= n || h[l] < 0 || h[l] >= n)
+      return fail(MCF_ERR_INVALID, "edge endpoint out of range");
+    if (t[l] == h[l]) return fail(MCF_ERR_INVALID, "self loops are not allowed");
+    keys[l] = (int64_t)t[l] * n + h[l];
+  }
+  std::sort(keys.begin(), keys.end());
+  if (std::adjacent_find(keys.begin(), keys.end()) != keys.end())
+    return fail(MCF_ERR_INVALID, "duplicate (tail, head) edge");
+  int rc = check_caps(m, cap);
+  if (rc != MCF_OK) return rc;
+  rc = check_weights(n, w);
+  if (rc != MCF_OK) return rc;
+  double gscalar = 0.5;
+  std::vector<double> gmat;
+  if (utility_kind == MCF_POW) {
+    if (!gamma || (gamma_len != 1 && gamma_len != (int64_t)n * n))
+      return fail(MCF_ERR_INVALID, "power utility needs gamma of length 1 or n*n");
+    if (gamma_len == 1) {
+      gscalar = gamma[0];
+      if (!(gscalar > 0.0 && gscalar < 1.0)) return fail(MCF_ERR_INVALID, "gamma must be in (0, 1)");
+    } else {
+      gmat.assign(gamma, gamma + (size_t)n * n);
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+          if (i != j && !(gmat[(size_t)i * n + j] > 0.0 && gmat[(size_t)i * n + j] < 1.0))
+            return fail(MCF_ERR_INVALID, "gamma must be in (0, 1)");
+    }
+  }
+  if (!strongly_connected(n, t, h))
+    return fail(MCF_ERR_NOT_CONNECTED, "network is not strongly connected");
+  mcf_problem* p = new mcf_problem();
+  p->n = n;
+  p->m = m;
+  p->kind = utility_kind;
+  p->tail = std::move(t);
+  p->head = std::move(h);
+  p->cap.assign(cap, cap + m);
+  p->w.assign(w, w + (size_t)n * n);
+  p->gamma_scalar = gscalar;
+  p->gamma_mat = std::move(gmat);
+  build_topology(n, p->tail, p->head, p->topo);
+  p->eta = 1.0 / std::sqrt(2.0 * (double)p->topo.dmax);   // Eq. (e-eta)
+  *out = p;
+  return MCF_OK;
+}
+
+int mcf_update_capacities(mcf_problem* p, const double* cap) {
+  if (!p) return fail(MCF_ERR_INVALID, "problem is NULL");
+  int rc = check_caps(p->m, cap);
+  if (rc != MCF_OK) return rc;
+  std::lock_guard<std::mutex> g(p->lock);
+  p->cap.assign(cap, cap + p->m);
+  p->data_dirty = true;
+  return MCF_OK;
+}
+
+int mcf_update_weights(mcf_problem* p, const double* w) {
+  if (!p) return fail(MCF_ERR_INVALID, "problem is NULL");
+  int rc = check_weights(p->n, w);
+  if (rc != MCF_OK) return rc;
+  std::lock_guard<std::mutex> g(p->lock);
+  p->w.assign(w, w + (size_t)p->n * p->n);
+  p->data_dirty = true;
+  return MCF_OK;
+}
+
+int mcf_destroy_problem(mcf_problem* p) {
+  if (!p) return MCF_OK;
+  if (p->busy.load() > 0) return fail(MCF_ERR_BUSY, "problem has a pending ticket");
+  {
+    std::lock_guard<std::mutex> g(p->lock);
+    device_free(p);
+  }
+  delete p;
+  return MCF_OK;
+}
+
+int mcf_problem_size(const mcf_problem* p, int32_t* n, int32_t* m) {
+  if (!p) return fail(MCF_ERR_INVALID, "problem is NULL");
+  if (n) *n = p->n;
+  if (m) *m = p->m;
+  return MCF_OK;
+}
+
+int64_t mcf_problem_device_bytes(const mcf_problem* p, int precision) {
+  if (!p) return fail(MCF_ERR_INVALID, "problem is NULL");
+  return device_bytes(p, precision);
+}
+
+static int solve_common(mcf_problem* p, const mcf_options* opts, mcf_result* res,
+                        mcf_kernel_times* kt) {
+  if (!p || !res) return fail(MCF_ERR_INVALID, "problem or result is NULL");
+  int rc = validate_options(opts);
+  if (rc != MCF_OK) return rc;
+  const auto t0 = std::chrono::steady_clock::now();
+  std::lock_guard<std::mutex> g(p->lock);
+  rc = device_solve(p, opts, res, kt);
+  res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (rc == MCF_OK || rc == MCF_ERR_NOT_CONVERGED || rc == MCF_ERR_NUMERIC) res->status = rc;
+  return rc;
+}
+
+int mcf_solve(mcf_problem* p, const mcf_options* opts, mcf_result* res) {
+  return solve_common(p, opts, res, nullptr);
+}
+
+int mcf_solve_timed(mcf_problem* p, const mcf_options* opts, mcf_result* res,
+                    mcf_kernel_times* kt) {
+  if (!kt) return fail(MCF_ERR_INVALID, "kernel times pointer is NULL");
+  return solve_common(p, opts, res, kt);
+}
+
+}  // extern "C"

@@ -1,0 +1,587 @@
+// pdmcf_device.cuh — sm_103a kernels of one PDMCF iteration (Zhang & Boyd, Algorithm 2.1).
+//
+// Layout in HBM (edge-major, so every per-edge or per-node vector is one coalesced
+// stream of 16-byte words):
+//   Ft[e][i]  = F_{i,l(e)}      m x ld, S (float | double | bf16), e = internal edge id
+//                               (edges sorted by head), ld = n rounded up to 8
+//   Yt[j][i]  = Y_{i,j}         n x ld, P (float | double)   — ping-pong pair
+//   Pt[j][i]  = (F A^T)_{i,j}   n x ld, P  — kept for the relaxation identity below
+//   Wt[j][i]  = w_{i,j}         n x ld, P
+// Pad entries i in [n, ld) are zero in every array and stay zero.
+//
+// One iteration k (Eq. e-pdhg-step, Algorithm 2.1 step 2) is three launches:
+//   edge_kernel   per edge l: q = f + alpha (Y_{:,head} - Y_{:,tail}), mu by Newton on
+//                 phi(mu) = sum (q - mu)_+ - c (the capped-simplex projection of Sec. 2.3),
+//                 f^ = (q - mu)_+, f_new = rho f^ + (1 - rho) f; FP64 partial of ||dF||^2.
+//   node_kernel   per node j: p = sum_{in(j)} f_new - sum_{out(j)} f_new = (F^{k+1/2}A^T)_{:,j},
+//                 F^ A^T = (p - (1-rho) P_old)/rho, F^{k+1} A^T = 2 F^ A^T - P_old,
+//                 v = Y_{:,j} - beta F^{k+1}A^T, Y^ = prox(v) (0 at i = j),
+//                 Y_new = rho Y^ + (1 - rho) Y; FP64 partial of ||dY||^2 and, on check
+//                 iterations, the objective/conjugate/consistency partials.
+//   scalar_kernel one block: fixed-order FP64 reductions, the primal weight rule of
+//                 Eq. (e-primal_weight), alpha/beta for the next iteration and, on check
+//                 iterations, r (Eq. e-res), the duality gap and the relative KKT measure.
+// plus check_kernel (per edge, check iterations only) for ||G||^2, <G, F^-Q>, ||F^-Q||^2
+// and the linear part of the dual bound.
+//
+// The F^{k+1} A^T identity: F^{k+1/2} = rho F^ + (1-rho) F^{k-1/2}, so
+// F^ A^T = (F^{k+1/2} A^T - (1-rho) F^{k-1/2} A^T) / rho and F^{k+1} = 2 F^ - F^{k-1/2};
+// the node phase therefore needs only the freshly written F^{k+1/2} rows and the n x n
+// state P = F^{k-1/2} A^T, never a stored F^{k+1}.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <math.h>
+
+#include "pdmcf_types.h"
+
+namespace pdmcf {
+
+// ------------------------------------------------------------------ element helpers
+
+template <typename S> struct StoreTraits;
+template <> struct StoreTraits<float>  { static constexpr int VW = 4; };
+template <> struct StoreTraits<double> { static constexpr int VW = 2; };
+template <> struct StoreTraits<__nv_bfloat16> { static constexpr int VW = 8; };
+
+template <typename P> __device__ __forceinline__ P to_p(float x) { return (P)x; }
+template <typename P> __device__ __forceinline__ P to_p(double x) { return (P)x; }
+template <typename P> __device__ __forceinline__ P to_p(__nv_bfloat16 x) { return (P)__bfloat162float(x); }
+
+template <typename S, typename P> __device__ __forceinline__ S from_p(P x);
+template <> __device__ __forceinline__ float from_p<float, float>(float x) { return x; }
+template <> __device__ __forceinline__ double from_p<double, double>(double x) { return x; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_p<__nv_bfloat16, float>(float x) {
+  return __float2bfloat16_rn(x);
+}
+
+// 16-byte vector loads/stores. "stream" = touched once per pass (evict-first in L2),
+// "keep" = read-only data that other CTAs re-read soon (default caching).
+template <typename T, int N>
+__device__ __forceinline__ void ld_keep(const T* p, T (&v)[N]) {
+  static_assert((N * sizeof(T)) % 16 == 0, "16-byte words");
+  constexpr int W = N * (int)sizeof(T) / 16;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    uint4 u = __ldg(reinterpret_cast<const uint4*>(p) + k);
+    memcpy(&v[k * 16 / sizeof(T)], &u, 16);
+  }
+}
+template <typename T, int N>
+__device__ __forceinline__ void ld_stream(const T* p, T (&v)[N]) {
+  constexpr int W = N * (int)sizeof(T) / 16;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    uint4 u = __ldcs(reinterpret_cast<const uint4*>(p) + k);
+    memcpy(&v[k * 16 / sizeof(T)], &u, 16);
+  }
+}
+template <typename T, int N>
+__device__ __forceinline__ void ld_plain(const T* p, T (&v)[N]) {
+  constexpr int W = N * (int)sizeof(T) / 16;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    uint4 u = *(reinterpret_cast<const uint4*>(p) + k);
+    memcpy(&v[k * 16 / sizeof(T)], &u, 16);
+  }
+}
+template <typename T, int N>
+__device__ __forceinline__ void st_stream(T* p, const T (&v)[N]) {
+  constexpr int W = N * (int)sizeof(T) / 16;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    uint4 u;
+    memcpy(&u, &v[k * 16 / sizeof(T)], 16);
+    __stcs(reinterpret_cast<uint4*>(p) + k, u);
+  }
+}
+template <typename T, int N>
+__device__ __forceinline__ void st_plain(T* p, const T (&v)[N]) {
+  constexpr int W = N * (int)sizeof(T) / 16;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    uint4 u;
+    memcpy(&u, &v[k * 16 / sizeof(T)], 16);
+    *(reinterpret_cast<uint4*>(p) + k) = u;
+  }
+}
+
+// ------------------------------------------------------------------ group reductions
+// A "group" is GROUP consecutive threads that own one edge (or node): a warp when
+// GROUP == 32, the whole block when GROUP == blockDim.x > 32. All threads of a group get
+// the same result (butterfly sums are commutative pairwise, so every lane sees the same
+// rounding; block sums read the per-warp partials in one fixed order).
+
+template <int GROUP> struct GroupScratch {
+  static constexpr int NW = GROUP > 32 ? GROUP / 32 : 1;
+  double s[2][NW];
+  int c[2][NW];
+  double x[2][NW];
+};
+
+template <int GROUP, typename P>
+__device__ __forceinline__ void group_sum_count(P& s, int& c, GroupScratch<GROUP>& sh, int& phase) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  if constexpr (GROUP > 32) {
+    constexpr int NW = GROUP / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sh.s[phase][warp] = (double)s; sh.c[phase][warp] = c; }
+    __syncthreads();
+    P ts = 0; int tc = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) { ts += (P)sh.s[phase][w]; tc += sh.c[phase][w]; }
+    s = ts; c = tc;
+    phase ^= 1;
+  }
+}
+
+template <int GROUP, typename P>
+__device__ __forceinline__ P group_max(P v, GroupScratch<GROUP>& sh, int& phase) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if constexpr (GROUP > 32) {
+    constexpr int NW = GROUP / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sh.x[phase][warp] = (double)v;
+    __syncthreads();
+    P t = (P)sh.x[phase][0];
+#pragma unroll
+    for (int w = 1; w < NW; ++w) t = fmax(t, (P)sh.x[phase][w]);
+    v = t;
+    phase ^= 1;
+  }
+  return v;
+}
+
+// Block-wide sum of K doubles per thread, written by thread 0 to out[0..K).
+template <int BLOCK, int K>
+__device__ __forceinline__ void block_sum_write(double (&v)[K], double* out) {
+  __shared__ double red[K][BLOCK / 32];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double t = 0.0;
+      for (int w = 0; w < BLOCK / 32; ++w) t += red[k][w];
+      out[k] = t;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ utilities (Sec. 1.1, 2.3)
+
+// prox_{beta (-u)^*}(y) for u = w log s: (y - sqrt(y^2 + 4 beta w))/2 (Sec. 2.3), evaluated
+// as -2 beta w / (y + sqrt(...)) when y > 0 to avoid cancellation (same value).
+template <typename P>
+__device__ __forceinline__ P prox_log(P y, P beta, P w) {
+  const P bw = beta * w;
+  const P s = sqrt(fma(y, y, P(4) * bw));
+  return y <= P(0) ? P(0.5) * (y - s) : (P(-2) * bw) / (y + s);
+}
+
+// prox_{beta (-u)^*}(y) for u = w s^gamma: z = -t, t the root of
+// h(t) = t^(c1+1) (t + y) - c1 c2 (Sec. 2.3), c1 = gamma/(1-gamma),
+// c2 = beta (1/gamma - 1)(w gamma)^(1/(1-gamma)). h is increasing and convex on
+// [max(0,-y), inf); Newton from t_hi = max(0,-y) + (c1 c2)^(1/(c1+2)) (where h >= 0)
+// decreases monotonically to the root. gamma = 1/2 (c1 = 1) avoids transcendental calls.
+template <typename P>
+__device__ __forceinline__ P prox_pow(P y, P beta, P w, P gamma) {
+  const P tlo = y < P(0) ? -y : P(0);
+  P t, k;
+  if (gamma == P(0.5)) {
+    k = beta * P(0.25) * w * w;                       // c1 c2 with c1 = 1
+    t = tlo + cbrt(k);
+#pragma unroll 1
+    for (int it = 0; it < 60; ++it) {
+      const P h = t * t * (t + y) - k;
+      const P dh = t * (P(3) * t + P(2) * y);
+      P tn = t - h / dh;
+      tn = tn < tlo ? tlo : tn;
+      if (!(tn < t)) break;
+      t = tn;
+    }
+  } else {
+    const P c1 = gamma / (P(1) - gamma);
+    k = c1 * beta * (P(1) / gamma - P(1)) * pow(w * gamma, P(1) / (P(1) - gamma));
+    t = tlo + pow(k, P(1) / (c1 + P(2)));
+#pragma unroll 1
+    for (int it = 0; it < 60; ++it) {
+      const P p = pow(t, c1);
+      const P h = p * t * (t + y) - k;
+      const P dh = p * ((c1 + P(2)) * t + (c1 + P(1)) * y);
+      P tn = t - h / dh;
+      tn = tn < tlo ? tlo : tn;
+      if (!(tn < t)) break;
+      t = tn;
+    }
+  }
+  return -t;
+}
+
+template <typename P>
+__device__ __forceinline__ P util_value(int kind, P t, P w, P g) {      // u(t)
+  return kind == 0 ? w * log(t) : w * pow(t, g);
+}
+template <typename P>
+__device__ __forceinline__ P util_grad(int kind, P t, P w, P g) {       // u'(t)
+  return kind == 0 ? w / t : w * g * pow(t, g - P(1));
+}
+// (-u)^*(y), y < 0: log: w log(w/(-y)) - w ; power: (1/g - 1)(w g)^(1/(1-g)) (-y)^(-g/(1-g))
+template <typename P>
+__device__ __forceinline__ P util_conj_neg(int kind, P y, P w, P g) {
+  if (kind == 0) return w * log(w / (-y)) - w;
+  return (P(1) / g - P(1)) * pow(w * g, P(1) / (P(1) - g)) * pow(-y, -g / (P(1) - g));
+}
+// (u')^{-1}(-y): the traffic whose marginal utility is -y
+template <typename P>
+__device__ __forceinline__ P util_traffic(int kind, P y, P w, P g) {
+  if (kind == 0) return w / (-y);
+  return pow(w * g / (-y), P(1) / (P(1) - g));
+}
+
+// ------------------------------------------------------------------ kernel arguments
+
+template <typename P, typename S>
+struct IterArgs {
+  int n, m, ld;
+  const int32_t* e_tail;
+  const int32_t* e_head;
+  const int32_t* in_ptr;
+  const int32_t* out_ptr;
+  const int32_t* out_idx;
+  const P* cap;
+  S* F[2];
+  P* Y[2];
+  P* Pm;
+  const P* W;
+  const P* Gm;        // per-pair gamma (n x ld) or nullptr
+  P gamma;            // scalar gamma when Gm == nullptr
+  int kind;           // 0 log, 1 power
+  P* mu;
+  P* That;
+  P* Uprime;
+  P* Yhat;
+  double* part_edge;  // [grid_edge]
+  double* part_node;  // [grid_node * NODE_PARTS]
+  double* part_check; // [grid_edge * CHECK_PARTS]
+  DevScalars* sc;
+  P rho;
+  int parity;         // F[parity], Y[parity] hold F^{k-1/2}, Y^k; the other slot receives k+1
+  int check;          // 1 on check iterations
+};
+
+// ------------------------------------------------------------------ projection
+
+// Capped-simplex projection of one column (Sec. 2.3): mu = 0 if sum (q)_+ <= c, else the
+// root of phi(mu) = sum_i (q_i - mu)_+ - c. phi is convex, decreasing and piecewise
+// linear, so Newton from a point left of the root, mu' = (sum_{q>mu} q - c)/#{q > mu},
+// rises monotonically and stops exactly when the active set {q > mu} no longer changes
+// (then mu = (sum_active q - c)/|active|, the value the sorted scan of Sec. 2.6 finds).
+// The previous iteration's mu is the starting point; if it lies right of the root, one
+// Newton step from there lands at or left of the root (tangents of a convex function lie
+// below it).
+template <int GROUP, int VPT, int VW, typename P>
+__device__ __forceinline__ P project_mu(const P (&q)[VPT][VW], P c, P mu0,
+                                        GroupScratch<GROUP>& sh, int& phase) {
+  auto eval = [&](P mu, P& s, int& cnt) {
+    P ls = 0; int lc = 0;
+#pragma unroll
+    for (int v = 0; v < VPT; ++v)
+#pragma unroll
+      for (int u = 0; u < VW; ++u)
+        if (q[v][u] > mu) { ls += q[v][u]; ++lc; }
+    group_sum_count<GROUP>(ls, lc, sh, phase);
+    s = ls; cnt = lc;
+  };
+  P mu = mu0 > P(0) ? mu0 : P(0);
+  P s; int cnt;
+  eval(mu, s, cnt);
+  P phi = s - (P)cnt * mu - c;
+  if (phi <= P(0)) {
+    if (mu == P(0) || phi == P(0)) return mu;           // mu* = 0, or exactly at the root
+    P mn = cnt > 0 ? (s - c) / (P)cnt : P(0);          // Newton step from the right
+    if (mn <= P(0)) {
+      mu = P(0);
+      eval(mu, s, cnt);
+      if (s - c <= P(0)) return P(0);
+    } else {
+      mu = mn;
+      eval(mu, s, cnt);
+    }
+  }
+#pragma unroll 1
+  for (int it = 0; it < 64; ++it) {
+    if (cnt == 0) break;
+    const P mn = (s - c) / (P)cnt;
+    if (!(mn > mu)) break;
+    const int prev = cnt;
+    mu = mn;
+    eval(mu, s, cnt);
+    if (cnt == prev) break;
+  }
+  return mu;
+}
+
+// ------------------------------------------------------------------ edge phase
+
+template <typename P, typename S, int VPT, int GROUP, int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB)
+edge_kernel(IterArgs<P, S> a) {
+  constexpr int VW = StoreTraits<S>::VW;
+  constexpr int GPB = BLOCK / GROUP;
+  __shared__ GroupScratch<GROUP> sh_all[GPB];
+  GroupScratch<GROUP>& sh = sh_all[threadIdx.x / GROUP];
+  int phase = 0;
+  const int lane = threadIdx.x % GROUP;
+  const int gid = blockIdx.x * GPB + threadIdx.x / GROUP;
+  const int ngroups = gridDim.x * GPB;
+  const int nchunks = a.ld / VW;
+  const P alpha = (P)a.sc->alpha;
+  const P rho = a.rho;
+  const S* __restrict__ Fo = a.F[a.parity];
+  S* __restrict__ Fn = a.F[a.parity ^ 1];
+  const P* __restrict__ Y = a.Y[a.parity];
+  double dsum = 0.0;
+
+  for (int e = gid; e < a.m; e += ngroups) {
+    const int h = a.e_head[e], t = a.e_tail[e];
+    const P c = a.cap[e];
+    const P mu0 = a.mu[e];
+    const S* fo = Fo + (size_t)e * a.ld;
+    const P* yh = Y + (size_t)h * a.ld;
+    const P* yt = Y + (size_t)t * a.ld;
+    P q[VPT][VW], f[VPT][VW];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      const int ci = v * GROUP + lane;
+      if (ci < nchunks) {
+        S fs[VW]; P a1[VW], a2[VW];
+        ld_stream<S, VW>(fo + ci * VW, fs);
+        ld_keep<P, VW>(yh + ci * VW, a1);
+        ld_keep<P, VW>(yt + ci * VW, a2);
+#pragma unroll
+        for (int u = 0; u < VW; ++u) {
+          f[v][u] = to_p<P>(fs[u]);
+          q[v][u] = f[v][u] + alpha * (a1[u] - a2[u]);
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < VW; ++u) { f[v][u] = P(0); q[v][u] = P(0); }
+      }
+    }
+    const P mu = project_mu<GROUP, VPT, VW, P>(q, c, mu0, sh, phase);
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      const int ci = v * GROUP + lane;
+      if (ci < nchunks) {
+        S out[VW];
+#pragma unroll
+        for (int u = 0; u < VW; ++u) {
+          const P fh = q[v][u] > mu ? q[v][u] - mu : P(0);
+          const P fnew = rho * fh + (P(1) - rho) * f[v][u];
+          out[u] = from_p<S, P>(fnew);
+          const double d = (double)(to_p<P>(out[u]) - f[v][u]);
+          dsum += d * d;
+        }
+        st_stream<S, VW>(Fn + (size_t)e * a.ld + ci * VW, out);
+      }
+    }
+    if (lane == 0) a.mu[e] = mu;
+  }
+  double v1[1] = {dsum};
+  block_sum_write<BLOCK, 1>(v1, a.part_edge + blockIdx.x);
+}
+
+// ------------------------------------------------------------------ node phase
+
+template <typename P, typename S, int VPT, int GROUP, int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB)
+node_kernel(IterArgs<P, S> a) {
+  constexpr int VW = StoreTraits<S>::VW;
+  constexpr int GPB = BLOCK / GROUP;
+  const int lane = threadIdx.x % GROUP;
+  const int gid = blockIdx.x * GPB + threadIdx.x / GROUP;
+  const int ngroups = gridDim.x * GPB;
+  const int nchunks = a.ld / VW;
+  const P beta = (P)a.sc->beta;
+  const P rho = a.rho;
+  const P inv_rho = P(1) / rho;
+  const S* __restrict__ Fn = a.F[a.parity ^ 1];
+  const P* __restrict__ Yo = a.Y[a.parity];
+  P* __restrict__ Yn = a.Y[a.parity ^ 1];
+  // partials: 0 ||dY||^2, 1 #nonpositive T, 2 sum u(T), 3 sum (-u)^*(Y^), 4 ||T(Y^)-T||^2,
+  //           5 ||T||^2, 6 #(Y^ >= 0 off-diagonal)
+  double acc[NODE_PARTS];
+#pragma unroll
+  for (int k = 0; k < NODE_PARTS; ++k) acc[k] = 0.0;
+
+  for (int j = gid; j < a.n; j += ngroups) {
+    P s[VPT][VW];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v)
+#pragma unroll
+      for (int u = 0; u < VW; ++u) s[v][u] = P(0);
+    const int ib = a.in_ptr[j], ie = a.in_ptr[j + 1];
+    for (int e = ib; e < ie; ++e) {
+      const S* fr = Fn + (size_t)e * a.ld;
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        const int ci = v * GROUP + lane;
+        if (ci < nchunks) {
+          S fs[VW];
+          ld_plain<S, VW>(fr + ci * VW, fs);
+#pragma unroll
+          for (int u = 0; u < VW; ++u) s[v][u] += to_p<P>(fs[u]);
+        }
+      }
+    }
+    const int ob = a.out_ptr[j], oe = a.out_ptr[j + 1];
+    for (int k = ob; k < oe; ++k) {
+      const S* fr = Fn + (size_t)a.out_idx[k] * a.ld;
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        const int ci = v * GROUP + lane;
+        if (ci < nchunks) {
+          S fs[VW];
+          ld_plain<S, VW>(fr + ci * VW, fs);
+#pragma unroll
+          for (int u = 0; u < VW; ++u) s[v][u] -= to_p<P>(fs[u]);
+        }
+      }
+    }
+    P* prow = a.Pm + (size_t)j * a.ld;
+    const P* yrow = Yo + (size_t)j * a.ld;
+    const P* wrow = a.W + (size_t)j * a.ld;
+    const P* grow = a.Gm ? a.Gm + (size_t)j * a.ld : nullptr;
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      const int ci = v * GROUP + lane;
+      if (ci >= nchunks) continue;
+      P po[VW], yo[VW], wv[VW], gv[VW], yn[VW];
+      ld_plain<P, VW>(prow + ci * VW, po);
+      ld_plain<P, VW>(yrow + ci * VW, yo);
+      ld_keep<P, VW>(wrow + ci * VW, wv);
+      if (grow) ld_keep<P, VW>(grow + ci * VW, gv);
+      else {
+#pragma unroll
+        for (int u = 0; u < VW; ++u) gv[u] = a.gamma;
+      }
+      P that_v[VW], up_v[VW], yh_v[VW];
+#pragma unroll
+      for (int u = 0; u < VW; ++u) {
+        const int i = ci * VW + u;
+        const P fhat_at = (s[v][u] - (P(1) - rho) * po[u]) * inv_rho;   // (F^ A^T)_{ij}
+        const P fplus_at = P(2) * fhat_at - po[u];                       // (F^{k+1} A^T)_{ij}
+        const bool live = (i < a.n) && (i != j);
+        P yhat = P(0);
+        if (live) {
+          const P vv = yo[u] - beta * fplus_at;
+          yhat = a.kind == 0 ? prox_log<P>(vv, beta, wv[u]) : prox_pow<P>(vv, beta, wv[u], gv[u]);
+        }
+        yn[u] = rho * yhat + (P(1) - rho) * yo[u];
+        const double dy = (double)(yn[u] - yo[u]);
+        acc[0] += dy * dy;
+        const P th = -fhat_at;
+        that_v[u] = i < a.n ? th : P(0);
+        yh_v[u] = yhat;
+        up_v[u] = P(0);
+        if (a.check && live) {
+          if (!(th > P(0))) acc[1] += 1.0;
+          else {
+            acc[2] += (double)util_value<P>(a.kind, th, wv[u], gv[u]);
+            up_v[u] = util_grad<P>(a.kind, th, wv[u], gv[u]);
+          }
+          if (yhat < P(0)) {
+            acc[3] += (double)util_conj_neg<P>(a.kind, yhat, wv[u], gv[u]);
+            const double dt = (double)util_traffic<P>(a.kind, yhat, wv[u], gv[u]) - (double)th;
+            acc[4] += dt * dt;
+          } else {
+            acc[6] += 1.0;
+          }
+          acc[5] += (double)th * (double)th;
+        }
+      }
+      st_plain<P, VW>(Yn + (size_t)j * a.ld + ci * VW, yn);
+      st_plain<P, VW>(prow + ci * VW, s[v]);
+      if (a.check) {
+        st_plain<P, VW>(a.That + (size_t)j * a.ld + ci * VW, that_v);
+        st_plain<P, VW>(a.Uprime + (size_t)j * a.ld + ci * VW, up_v);
+        st_plain<P, VW>(a.Yhat + (size_t)j * a.ld + ci * VW, yh_v);
+      }
+    }
+  }
+  block_sum_write<BLOCK, NODE_PARTS>(acc, a.part_node + (size_t)blockIdx.x * NODE_PARTS);
+}
+
+// ------------------------------------------------------------------ check (residual) phase
+// Per edge: Q column from F^{k-1/2} and Y^k, F^ = (q - mu)_+ with the mu just computed,
+// D = F^ - Q, G = U'_{:,head} - U'_{:,tail}; partial sums of ||G||^2, <G,D>, ||D||^2
+// (Eq. e-res) and c_l max(0, max_i (Y^ A)_il) for the dual bound.
+template <typename P, typename S, int VPT, int GROUP, int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB)
+check_kernel(IterArgs<P, S> a) {
+  constexpr int VW = StoreTraits<S>::VW;
+  constexpr int GPB = BLOCK / GROUP;
+  __shared__ GroupScratch<GROUP> sh_all[GPB];
+  GroupScratch<GROUP>& sh = sh_all[threadIdx.x / GROUP];
+  int phase = 0;
+  const int lane = threadIdx.x % GROUP;
+  const int gid = blockIdx.x * GPB + threadIdx.x / GROUP;
+  const int ngroups = gridDim.x * GPB;
+  const int nchunks = a.ld / VW;
+  const P alpha = (P)a.sc->alpha;
+  const S* __restrict__ Fo = a.F[a.parity];
+  const P* __restrict__ Y = a.Y[a.parity];
+  double acc[CHECK_PARTS] = {0.0, 0.0, 0.0, 0.0};
+  for (int e = gid; e < a.m; e += ngroups) {
+    const int h = a.e_head[e], t = a.e_tail[e];
+    const P mu = a.mu[e];
+    const size_t fo = (size_t)e * a.ld, ho = (size_t)h * a.ld, to = (size_t)t * a.ld;
+    P ymax = -INFINITY;
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      const int ci = v * GROUP + lane;
+      if (ci >= nchunks) continue;
+      S fs[VW];
+      P y1[VW], y2[VW], g1[VW], g2[VW], z1[VW], z2[VW];
+      ld_plain<S, VW>(Fo + fo + ci * VW, fs);
+      ld_keep<P, VW>(Y + ho + ci * VW, y1);
+      ld_keep<P, VW>(Y + to + ci * VW, y2);
+      ld_keep<P, VW>(a.Uprime + ho + ci * VW, g1);
+      ld_keep<P, VW>(a.Uprime + to + ci * VW, g2);
+      ld_keep<P, VW>(a.Yhat + ho + ci * VW, z1);
+      ld_keep<P, VW>(a.Yhat + to + ci * VW, z2);
+#pragma unroll
+      for (int u = 0; u < VW; ++u) {
+        const int i = ci * VW + u;
+        if (i >= a.n) continue;
+        const P q = to_p<P>(fs[u]) + alpha * (y1[u] - y2[u]);
+        const P fh = q > mu ? q - mu : P(0);
+        const double d = (double)fh - (double)q;
+        const double g = (double)g1[u] - (double)g2[u];
+        acc[0] += g * g;
+        acc[1] += g * d;
+        acc[2] += d * d;
+        ymax = fmax(ymax, z1[u] - z2[u]);
+      }
+    }
+    ymax = group_max<GROUP, P>(ymax, sh, phase);
+    if (lane == 0 && ymax > P(0)) acc[3] += (double)a.cap[e] * (double)ymax;
+  }
+  block_sum_write<BLOCK, CHECK_PARTS>(acc, a.part_check + (size_t)blockIdx.x * CHECK_PARTS);
+}
+
+}  // namespace pdmcf

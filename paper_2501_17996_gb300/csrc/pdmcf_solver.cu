@@ -1,0 +1,750 @@
+// pdmcf_solver.cu — host driver of the PDMCF iteration on one GPU.
+//
+// Owns the device state of a problem (iterates, incidence, data, reduction scratch),
+// launches one iteration as edge -> node -> [check] -> scalar kernels, groups k_check
+// iterations into a CUDA graph whose last iteration evaluates the stop test quantities,
+// and reads the FP64 scalars back once per chunk (Algorithm 2.1, step 1, evaluated every
+// k_check iterations).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "pdmcf_internal.h"
+#include "pdmcf_kernels.h"
+
+namespace pdmcf {
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      set_error(std::string("CUDA error ") + cudaGetErrorString(e_) + " in " #call);   \
+      return MCF_ERR_CUDA;                                                             \
+    }                                                                                  \
+  } while (0)
+
+// ------------------------------------------------------------------ scalar tail kernel
+
+struct ScalarArgs {
+  DevScalars* sc;
+  const double* pe;
+  int nbe;
+  const double* pn;
+  int nbn;
+  const double* pc;
+  int nbc;
+  int check;
+};
+
+// Deterministic sum of base[b*stride + field] over b < nb by 256 threads: contiguous
+// per-thread segments, then a fixed binary tree.
+__device__ double det_sum(const double* base, int nb, int stride, int field, double* sh) {
+  const int per = (nb + 255) / 256;
+  const int b0 = threadIdx.x * per;
+  const int b1 = min(nb, b0 + per);
+  double s = 0.0;
+  for (int b = b0; b < b1; ++b) s += base[(size_t)b * stride + field];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(256) scalar_kernel(ScalarArgs a) {
+  __shared__ double sh[256];
+  const double dF2 = det_sum(a.pe, a.nbe, 1, 0, sh);
+  const double dY2 = det_sum(a.pn, a.nbn, NODE_PARTS, 0, sh);
+  double nodep[NODE_PARTS];
+  double chk[CHECK_PARTS];
+  if (a.check) {
+    for (int f = 1; f < NODE_PARTS; ++f) nodep[f] = det_sum(a.pn, a.nbn, NODE_PARTS, f, sh);
+    for (int f = 0; f < CHECK_PARTS; ++f) chk[f] = det_sum(a.pc, a.nbc, CHECK_PARTS, f, sh);
+  }
+  if (threadIdx.x != 0) return;
+  DevScalars* s = a.sc;
+  const double inf = INFINITY;
+  const double dF = sqrt(dF2), dY = sqrt(dY2);
+  s->dF = dF;
+  s->dY = dY;
+  if (!isfinite(dF) || !isfinite(dY)) s->numeric_error = 1;
+  const long long k = s->k;
+  if (a.check) {
+    const double nonpos = nodep[1], Psum = nodep[2], conj = nodep[3], cons2 = nodep[4];
+    const double t2 = nodep[5], ybad = nodep[6];
+    const double g2 = chk[0], gd = chk[1], d2 = chk[2], lin = chk[3];
+    const bool feasible = nonpos == 0.0;
+    // Eq. (e-res): r = ||G||^2 - <G,D>^2/||D||^2 if D != 0 and <G,D> >= 0, else ||G||^2
+    double r = inf;
+    if (feasible) {
+      r = (d2 == 0.0 || gd < 0.0) ? g2 : g2 - gd * gd / d2;
+      if (r < 0.0) r = 0.0;
+    }
+    const double P = feasible ? Psum : -inf;
+    const double D = ybad > 0.0 ? inf : conj + lin;
+    s->feasible = feasible ? 1 : 0;
+    s->r = r;
+    s->P = P;
+    s->D = D;
+    s->g_norm = sqrt(g2);
+    s->rel_gap = (feasible && isfinite(D)) ? (D - P) / (1.0 + fabs(P) + fabs(D)) : inf;
+    s->rel_cons = ybad > 0.0 ? inf : sqrt(cons2) / (1.0 + sqrt(t2));
+    s->rel_stat = feasible ? sqrt(r) / (1.0 + sqrt(g2)) : inf;
+    s->rel_kkt = fmax(s->rel_gap, fmax(s->rel_cons, s->rel_stat));
+    s->nonpos_frac = nonpos / ((double)s->n * (double)(s->n - 1));
+    s->check_k = k + 1;
+    if (!isfinite(Psum) && feasible) s->numeric_error = 1;
+  }
+  // Algorithm 2.1, step 3 (Eq. e-primal_weight)
+  s->alpha_last = s->alpha;
+  s->beta_last = s->beta;
+  if (k % s->k_adapt == 0 && dF > s->tau && dY > s->tau && (s->freeze < 0 || k < s->freeze)) {
+    s->omega = pow(dY / dF, s->theta) * pow(s->omega, 1.0 - s->theta);
+  }
+  s->alpha = s->eta / s->omega;
+  s->beta = s->eta * s->omega;
+  s->k = k + 1;
+}
+
+// ------------------------------------------------------------------ init / output kernels
+
+// Y^0 = I - 1 1^T (Sec. 2.5): 0 on the diagonal, -1 elsewhere; pads 0.
+template <typename P>
+__global__ void init_y_kernel(P* Y, int n, int ld) {
+  const size_t total = (size_t)n * ld;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / ld), i = (int)(idx % ld);
+    Y[idx] = (i < n && i != j) ? P(-1) : P(0);
+  }
+}
+
+// F^ = (q - mu)_+ with q = F^{k-3/2} + alpha_last (Y^{k-1}_{:,h} - Y^{k-1}_{:,t}): the
+// projected flow the last iteration computed (Algorithm 2.1 returns F^{k-1/2}).
+template <typename P, typename S>
+__global__ void fhat_kernel(const S* Fo, const P* Y, const int32_t* et, const int32_t* eh,
+                            const P* mu, const DevScalars* sc, P* out, int m, int ld) {
+  const P alpha = (P)sc->alpha_last;
+  const size_t total = (size_t)m * ld;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int e = (int)(idx / ld), i = (int)(idx % ld);
+    const P q = to_p<P>(Fo[idx]) + alpha * (Y[(size_t)eh[e] * ld + i] - Y[(size_t)et[e] * ld + i]);
+    out[idx] = q > mu[e] ? q - mu[e] : P(0);
+  }
+}
+
+// ------------------------------------------------------------------ device state
+
+struct DeviceState {
+  int device = -1, precision = -1;
+  int n = 0, m = 0, ld = 0;
+  size_t sbytes = 0, pbytes = 0;
+  void* F[2] = {nullptr, nullptr};
+  void* Y[2] = {nullptr, nullptr};
+  void *Pm = nullptr, *W = nullptr, *G = nullptr, *mu = nullptr, *cap = nullptr;
+  void *That = nullptr, *Uprime = nullptr, *Yhat = nullptr;
+  int32_t *e_tail = nullptr, *e_head = nullptr, *in_ptr = nullptr, *out_ptr = nullptr,
+          *out_idx = nullptr;
+  double *part_edge = nullptr, *part_node = nullptr, *part_check = nullptr;
+  DevScalars* sc = nullptr;
+  DevScalars* sc_host = nullptr;
+  cudaStream_t own_stream = nullptr;
+  int shape = -1, auto_shape = -1, block = 0, grid_edge = 0, grid_node = 0, grid_check = 0;
+  int cur = 0;
+  bool valid = false;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int graph_len = 0;
+  double graph_rho = 0.0;
+  cudaStream_t graph_stream = nullptr;
+  bool graphs_broken = false;
+};
+
+template <typename P, typename S> const KernelTable<P, S>& get_table();
+template <> const KernelTable<float, float>& get_table<float, float>() {
+  static const KernelTable<float, float> t = [] {
+    KernelTable<float, float> t{};
+    fill_f32_0(t); fill_f32_1(t); fill_f32_2(t); fill_f32_3(t); fill_f32_4(t);
+    return t;
+  }();
+  return t;
+}
+template <> const KernelTable<double, double>& get_table<double, double>() {
+  static const KernelTable<double, double> t = [] {
+    KernelTable<double, double> t{};
+    fill_f64_0(t); fill_f64_1(t); fill_f64_2(t); fill_f64_3(t); fill_f64_4(t);
+    return t;
+  }();
+  return t;
+}
+template <> const KernelTable<float, __nv_bfloat16>& get_table<float, __nv_bfloat16>() {
+  static const KernelTable<float, __nv_bfloat16> t = [] {
+    KernelTable<float, __nv_bfloat16> t{};
+    fill_bf16_0(t); fill_bf16_1(t); fill_bf16_2(t); fill_bf16_3(t); fill_bf16_4(t);
+    return t;
+  }();
+  return t;
+}
+
+static void destroy_graphs(DeviceState* d) {
+  for (int i = 0; i < 2; ++i)
+    if (d->graph[i]) { cudaGraphExecDestroy(d->graph[i]); d->graph[i] = nullptr; }
+  d->graph_len = 0;
+}
+
+static void free_state(DeviceState* d) {
+  if (!d) return;
+  cudaSetDevice(d->device);
+  destroy_graphs(d);
+  void* bufs[] = {d->F[0], d->F[1], d->Y[0], d->Y[1], d->Pm, d->W, d->G, d->mu, d->cap,
+                  d->That, d->Uprime, d->Yhat, d->e_tail, d->e_head, d->in_ptr,
+                  d->out_ptr, d->out_idx, d->part_edge, d->part_node, d->part_check, d->sc};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (d->sc_host) cudaFreeHost(d->sc_host);
+  if (d->own_stream) cudaStreamDestroy(d->own_stream);
+  delete d;
+}
+
+static size_t ld_of(int n) { return (size_t)((n + 7) / 8 * 8); }
+
+static size_t elem_bytes_f(int precision) {
+  return precision == MCF_FP64 ? 8 : (precision == MCF_BF16_F ? 2 : 4);
+}
+static size_t elem_bytes_p(int precision) { return precision == MCF_FP64 ? 8 : 4; }
+
+int64_t device_bytes(const mcf_problem* p, int precision) {
+  const size_t ld = ld_of(p->n), n = p->n, m = p->m;
+  const size_t sf = elem_bytes_f(precision), sp = elem_bytes_p(precision);
+  size_t b = 2 * m * ld * sf;                       // F ping-pong
+  b += 2 * n * ld * sp;                             // Y ping-pong
+  b += (3 + (p->gamma_mat.empty() ? 0 : 1)) * n * ld * sp;   // P, W, [gamma], T^ (+below)
+  b += 2 * n * ld * sp;                             // U', Y^
+  b += 2 * m * sp + (3 * m + 2 * (n + 1)) * 4;      // mu, cap, incidence
+  b += 64 * 1024;                                   // partials, scalars
+  return (int64_t)b;
+}
+
+// Upload c, w (transposed to Wt[j][i] = w_ij) and per-pair gamma in precision P.
+template <typename P>
+static int upload_data(mcf_problem* p, DeviceState* d, cudaStream_t st) {
+  const int n = p->n, m = p->m, ld = d->ld;
+  std::vector<P> cap(m);
+  for (int e = 0; e < m; ++e) cap[e] = (P)p->cap[p->topo.perm[e]];
+  CK(cudaMemcpyAsync(d->cap, cap.data(), m * sizeof(P), cudaMemcpyHostToDevice, st));
+  std::vector<P> wt((size_t)n * ld, P(0));
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i)
+      if (i != j) wt[(size_t)j * ld + i] = (P)p->w[(size_t)i * n + j];
+  CK(cudaMemcpyAsync(d->W, wt.data(), wt.size() * sizeof(P), cudaMemcpyHostToDevice, st));
+  if (d->G) {
+    for (int j = 0; j < n; ++j)
+      for (int i = 0; i < n; ++i)
+        wt[(size_t)j * ld + i] = (i != j) ? (P)p->gamma_mat[(size_t)i * n + j] : P(0.5);
+    CK(cudaMemcpyAsync(d->G, wt.data(), wt.size() * sizeof(P), cudaMemcpyHostToDevice, st));
+  }
+  CK(cudaStreamSynchronize(st));   // host staging vectors die at return
+  p->data_dirty = false;
+  return MCF_OK;
+}
+
+int mcf_shape_count() { return NUM_SHAPES; }
+
+template <typename P, typename S>
+static int setup_grids(DeviceState* d, int want) {
+  const KernelTable<P, S>& T = get_table<P, S>();
+  constexpr int VW = StoreTraits<S>::VW;
+  const int nchunks = (int)(d->ld / VW);
+  const int shape = want >= 0 ? want : pick_shape(nchunks);
+  if (shape < 0 || T.edge[shape] == nullptr ||
+      kShapes[shape].group * kShapes[shape].vpt < nchunks) {
+    set_error("no kernel shape covers this problem size at this precision");
+    return MCF_ERR_INVALID;
+  }
+  d->shape = shape;
+  d->auto_shape = pick_shape(nchunks);
+  const ShapeDesc sd = kShapes[d->shape];
+  d->block = sd.block;
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d->device));
+  int oe = 0, on = 0, oc = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oe, (const void*)T.edge[d->shape], sd.block, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&on, (const void*)T.node[d->shape], sd.block, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, (const void*)T.check[d->shape], sd.block, 0));
+  const int gpb = sd.block / sd.group;
+  auto grid = [&](int items, int occ) {
+    const int need = (items + gpb - 1) / gpb;
+    return std::max(1, std::min(need, std::max(1, occ) * sms));
+  };
+  d->grid_edge = grid(d->m, oe);
+  d->grid_node = grid(d->n, on);
+  d->grid_check = grid(d->m, oc);
+  return MCF_OK;
+}
+
+static int configure_shape(DeviceState* d, int want) {
+  if (d->precision == MCF_FP64) return setup_grids<double, double>(d, want);
+  if (d->precision == MCF_BF16_F) return setup_grids<float, __nv_bfloat16>(d, want);
+  return setup_grids<float, float>(d, want);
+}
+
+// (Re)allocate the per-block partial arrays for the current grids.
+static int alloc_partials(DeviceState* d) {
+  for (double** b : {&d->part_edge, &d->part_node, &d->part_check})
+    if (*b) { cudaFree(*b); *b = nullptr; }
+  bool ok = cudaMalloc((void**)&d->part_edge, (size_t)std::max(d->grid_edge, 1) * sizeof(double)) == cudaSuccess &&
+            cudaMalloc((void**)&d->part_node, (size_t)std::max(d->grid_node, 1) * NODE_PARTS * sizeof(double)) == cudaSuccess &&
+            cudaMalloc((void**)&d->part_check, (size_t)std::max(d->grid_check, 1) * CHECK_PARTS * sizeof(double)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    set_error("device allocation failed");
+    return MCF_ERR_OOM;
+  }
+  return MCF_OK;
+}
+
+static int alloc_state(mcf_problem* p, int precision, int device, int shape, cudaStream_t st_hint,
+                       DeviceState** out) {
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) {
+    set_error("no CUDA device available (the solver has no CPU path)");
+    return MCF_ERR_CUDA;
+  }
+  if (device < 0 || device >= ndev) {
+    set_error("invalid CUDA device ordinal");
+    return MCF_ERR_INVALID;
+  }
+  CK(cudaSetDevice(device));
+  DeviceState* d = new DeviceState();
+  d->device = device;
+  d->precision = precision;
+  d->n = p->n;
+  d->m = p->m;
+  d->ld = (int)ld_of(p->n);
+  d->sbytes = elem_bytes_f(precision);
+  d->pbytes = elem_bytes_p(precision);
+  int rc = configure_shape(d, shape);
+  if (rc != MCF_OK) { free_state(d); return rc; }
+  const size_t n = d->n, m = d->m, ld = d->ld;
+  auto A = [&](void** ptr, size_t bytes) -> bool {
+    if (cudaMalloc(ptr, bytes) != cudaSuccess) { cudaGetLastError(); return false; }
+    return true;
+  };
+  bool ok = true;
+  for (int i = 0; i < 2 && ok; ++i) ok = A(&d->F[i], m * ld * d->sbytes) && A(&d->Y[i], n * ld * d->pbytes);
+  ok = ok && A(&d->Pm, n * ld * d->pbytes) && A(&d->W, n * ld * d->pbytes) &&
+       A(&d->That, n * ld * d->pbytes) && A(&d->Uprime, n * ld * d->pbytes) &&
+       A(&d->Yhat, n * ld * d->pbytes) && A(&d->mu, m * d->pbytes) && A(&d->cap, m * d->pbytes);
+  if (ok && !p->gamma_mat.empty()) ok = A(&d->G, n * ld * d->pbytes);
+  ok = ok && A((void**)&d->e_tail, m * 4) && A((void**)&d->e_head, m * 4) &&
+       A((void**)&d->in_ptr, (n + 1) * 4) && A((void**)&d->out_ptr, (n + 1) * 4) &&
+       A((void**)&d->out_idx, m * 4);
+  ok = ok && A((void**)&d->sc, sizeof(DevScalars)) && alloc_partials(d) == MCF_OK;
+  if (!ok) {
+    free_state(d);
+    set_error("device allocation failed");
+    return MCF_ERR_OOM;
+  }
+  if (cudaMallocHost((void**)&d->sc_host, sizeof(DevScalars)) != cudaSuccess) {
+    free_state(d);
+    set_error("pinned host allocation failed");
+    return MCF_ERR_OOM;
+  }
+  if (cudaStreamCreateWithFlags(&d->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    free_state(d);
+    set_error("stream creation failed");
+    return MCF_ERR_CUDA;
+  }
+  cudaStream_t st = st_hint ? st_hint : d->own_stream;
+  const Topology& t = p->topo;
+  CK(cudaMemcpyAsync(d->e_tail, t.e_tail.data(), m * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d->e_head, t.e_head.data(), m * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d->in_ptr, t.in_ptr.data(), (n + 1) * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d->out_ptr, t.out_ptr.data(), (n + 1) * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d->out_idx, t.out_idx.data(), m * 4, cudaMemcpyHostToDevice, st));
+  // the kernels read every chunk of every row, so pads must start at zero everywhere
+  for (void* b : {d->That, d->Uprime, d->Yhat}) CK(cudaMemsetAsync(b, 0, n * ld * d->pbytes, st));
+  CK(cudaStreamSynchronize(st));
+  p->data_dirty = true;
+  *out = d;
+  return MCF_OK;
+}
+
+void device_free(mcf_problem* p) {
+  free_state(p->ds);
+  p->ds = nullptr;
+}
+
+// ------------------------------------------------------------------ iteration
+
+template <typename P, typename S>
+static IterArgs<P, S> make_args(DeviceState* d, const mcf_problem* p, double rho) {
+  IterArgs<P, S> a{};
+  a.n = d->n;
+  a.m = d->m;
+  a.ld = d->ld;
+  a.e_tail = d->e_tail;
+  a.e_head = d->e_head;
+  a.in_ptr = d->in_ptr;
+  a.out_ptr = d->out_ptr;
+  a.out_idx = d->out_idx;
+  a.cap = (const P*)d->cap;
+  a.F[0] = (S*)d->F[0];
+  a.F[1] = (S*)d->F[1];
+  a.Y[0] = (P*)d->Y[0];
+  a.Y[1] = (P*)d->Y[1];
+  a.Pm = (P*)d->Pm;
+  a.W = (const P*)d->W;
+  a.Gm = (const P*)d->G;
+  a.gamma = (P)p->gamma_scalar;
+  a.kind = p->kind;
+  a.mu = (P*)d->mu;
+  a.That = (P*)d->That;
+  a.Uprime = (P*)d->Uprime;
+  a.Yhat = (P*)d->Yhat;
+  a.part_edge = d->part_edge;
+  a.part_node = d->part_node;
+  a.part_check = d->part_check;
+  a.sc = d->sc;
+  a.rho = (P)rho;
+  return a;
+}
+
+template <typename P, typename S>
+static cudaError_t launch_iteration(DeviceState* d, IterArgs<P, S> a, int parity, bool check,
+                                    cudaStream_t st) {
+  const KernelTable<P, S>& T = get_table<P, S>();
+  a.parity = parity;
+  a.check = check ? 1 : 0;
+  void* kargs[] = {&a};
+  cudaError_t e;
+  e = cudaLaunchKernel((const void*)T.edge[d->shape], dim3(d->grid_edge), dim3(d->block), kargs, 0, st);
+  if (e != cudaSuccess) return e;
+  e = cudaLaunchKernel((const void*)T.node[d->shape], dim3(d->grid_node), dim3(d->block), kargs, 0, st);
+  if (e != cudaSuccess) return e;
+  if (check) {
+    e = cudaLaunchKernel((const void*)T.check[d->shape], dim3(d->grid_check), dim3(d->block), kargs, 0, st);
+    if (e != cudaSuccess) return e;
+  }
+  ScalarArgs sa{d->sc, d->part_edge, d->grid_edge, d->part_node, d->grid_node,
+                d->part_check, d->grid_check, check ? 1 : 0};
+  scalar_kernel<<<1, 256, 0, st>>>(sa);
+  return cudaGetLastError();
+}
+
+// One iteration with a CUDA event before the first and after every kernel (on st).
+struct EventPool {
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> kind;   // kernel kind that ends at event i (i >= 1)
+  size_t used = 0;
+  cudaEvent_t next(int k) {
+    if (used == ev.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      ev.push_back(e);
+      kind.push_back(-1);
+    }
+    kind[used] = k;
+    return ev[used++];
+  }
+  ~EventPool() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+};
+
+template <typename P, typename S>
+static cudaError_t launch_iteration_timed(DeviceState* d, IterArgs<P, S> a, int parity, bool check,
+                                          cudaStream_t st, EventPool& pool) {
+  const KernelTable<P, S>& T = get_table<P, S>();
+  a.parity = parity;
+  a.check = check ? 1 : 0;
+  void* kargs[] = {&a};
+  cudaError_t e;
+  if (pool.used == 0) cudaEventRecord(pool.next(-1), st);
+  e = cudaLaunchKernel((const void*)T.edge[d->shape], dim3(d->grid_edge), dim3(d->block), kargs, 0, st);
+  if (e != cudaSuccess) return e;
+  cudaEventRecord(pool.next(0), st);
+  e = cudaLaunchKernel((const void*)T.node[d->shape], dim3(d->grid_node), dim3(d->block), kargs, 0, st);
+  if (e != cudaSuccess) return e;
+  cudaEventRecord(pool.next(1), st);
+  if (check) {
+    e = cudaLaunchKernel((const void*)T.check[d->shape], dim3(d->grid_check), dim3(d->block), kargs, 0, st);
+    if (e != cudaSuccess) return e;
+    cudaEventRecord(pool.next(2), st);
+  }
+  ScalarArgs sa{d->sc, d->part_edge, d->grid_edge, d->part_node, d->grid_node,
+                d->part_check, d->grid_check, check ? 1 : 0};
+  scalar_kernel<<<1, 256, 0, st>>>(sa);
+  cudaEventRecord(pool.next(3), st);
+  return cudaGetLastError();
+}
+
+// Add the event intervals of a synchronized chunk to kt and reset the pool.
+static void drain_events(EventPool& pool, mcf_kernel_times* kt) {
+  for (size_t i = 1; i < pool.used; ++i) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, pool.ev[i - 1], pool.ev[i]);
+    kt->ms[pool.kind[i]] += ms;
+    kt->launches[pool.kind[i]] += 1;
+    kt->ms_total += ms;
+  }
+  pool.used = 0;
+}
+
+// Capture k_check iterations starting at the given parity, the last one a check.
+template <typename P, typename S>
+static bool capture_chunk(DeviceState* d, const IterArgs<P, S>& a, int parity, int len,
+                          cudaStream_t st, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  bool ok = true;
+  int par = parity;
+  for (int i = 0; i < len && ok; ++i) {
+    ok = launch_iteration<P, S>(d, a, par, i == len - 1, st) == cudaSuccess;
+    par ^= 1;
+  }
+  const cudaError_t e = cudaStreamEndCapture(st, &g);
+  if (!ok || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return false;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return true;
+}
+
+static void fill_scalars(const DevScalars& s, const mcf_problem* p, mcf_result* res) {
+  res->iters = s.k;
+  res->feasible = s.feasible;
+  res->utility = s.P;
+  res->dual_bound = s.D;
+  res->r = s.r;
+  res->r_over_nm = s.r / ((double)p->n * (double)p->m);
+  res->rel_gap = s.rel_gap;
+  res->rel_cons = s.rel_cons;
+  res->rel_stat = s.rel_stat;
+  res->rel_kkt = s.rel_kkt;
+  res->nonpos_frac = s.nonpos_frac;
+  res->omega = s.omega;
+}
+
+template <typename P, typename S>
+static int solve_t(mcf_problem* p, DeviceState* d, const mcf_options* o, mcf_result* res,
+                   cudaStream_t st, mcf_kernel_times* kt) {
+  const int n = d->n;
+  const size_t ld = d->ld, m = d->m;
+  if (p->data_dirty) {
+    int rc = upload_data<P>(p, d, st);
+    if (rc != MCF_OK) return rc;
+  }
+  const bool warm = o->warm_start && d->valid;
+  DevScalars& h = *d->sc_host;
+  if (!warm) {
+    d->cur = 0;
+    CK(cudaMemsetAsync(d->F[0], 0, m * ld * d->sbytes, st));
+    CK(cudaMemsetAsync(d->F[1], 0, m * ld * d->sbytes, st));
+    CK(cudaMemsetAsync(d->Pm, 0, (size_t)n * ld * d->pbytes, st));
+    CK(cudaMemsetAsync(d->mu, 0, m * d->pbytes, st));
+    init_y_kernel<P><<<1024, 256, 0, st>>>((P*)d->Y[0], n, (int)ld);
+    CK(cudaGetLastError());
+    p->omega = o->omega0 > 0 ? o->omega0 : 1.0;
+  }
+  std::memset(&h, 0, sizeof(DevScalars));
+  h.eta = p->eta;
+  h.omega = p->omega;
+  h.alpha = h.eta / h.omega;
+  h.beta = h.eta * h.omega;
+  h.alpha_last = h.alpha;
+  h.beta_last = h.beta;
+  h.k = 0;
+  h.theta = o->theta;
+  h.tau = o->tau;
+  h.k_adapt = o->k_adapt > 0 ? o->k_adapt : 1;
+  h.freeze = o->omega_freeze_iter;
+  h.r = INFINITY;
+  h.rel_kkt = INFINITY;
+  h.n = n;
+  h.m = (int)m;
+  CK(cudaMemcpyAsync(d->sc, &h, sizeof(DevScalars), cudaMemcpyHostToDevice, st));
+
+  const IterArgs<P, S> args = make_args<P, S>(d, p, o->rho);
+  const int64_t max_iters = o->max_iters;
+  const int kc = std::max(1, o->k_check);
+  bool use_graphs = o->use_graphs && !d->graphs_broken && kt == nullptr;
+  EventPool pool;
+  if (kt) std::memset(kt, 0, sizeof(*kt));
+  if (use_graphs && (d->graph_len != kc || d->graph_rho != o->rho || d->graph_stream != st)) {
+    destroy_graphs(d);
+    d->graph_len = kc;
+    d->graph_rho = o->rho;
+    d->graph_stream = st;
+  }
+  int parity = d->cur;
+  int64_t k = 0;
+  int status = MCF_ERR_NOT_CONVERGED;
+  if (o->stop_mode == MCF_STOP_NONE) status = MCF_OK;
+  bool any = false;
+  while (k < max_iters) {
+    const int64_t chunk = std::min<int64_t>(kc - (k % kc), max_iters - k);
+    if (use_graphs && chunk == kc) {
+      if (!d->graph[parity] && !capture_chunk<P, S>(d, args, parity, kc, st, &d->graph[parity])) {
+        d->graphs_broken = true;
+        use_graphs = false;
+      }
+    }
+    if (use_graphs && chunk == kc) {
+      CK(cudaGraphLaunch(d->graph[parity], st));
+      if (kc & 1) parity ^= 1;
+    } else {
+      for (int64_t i = 0; i < chunk; ++i) {
+        if (kt) CK((launch_iteration_timed<P, S>(d, args, parity, i == chunk - 1, st, pool)));
+        else CK((launch_iteration<P, S>(d, args, parity, i == chunk - 1, st)));
+        parity ^= 1;
+      }
+    }
+    CK(cudaMemcpyAsync(d->sc_host, d->sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (kt) drain_events(pool, kt);
+    k += chunk;
+    any = true;
+    d->cur = parity;
+    d->valid = true;
+    if (h.numeric_error) {
+      status = MCF_ERR_NUMERIC;
+      set_error("NaN or Inf in the iterates");
+      break;
+    }
+    if (o->stop_mode == MCF_STOP_PAPER && h.r < (double)n * (double)m * o->eps) { status = MCF_OK; break; }
+    if (o->stop_mode == MCF_STOP_REL_KKT && h.rel_kkt < o->eps) { status = MCF_OK; break; }
+  }
+  p->omega = h.omega;
+  if (!any) {
+    set_error("max_iters must be >= 1");
+    return MCF_ERR_INVALID;
+  }
+  fill_scalars(h, p, res);
+  res->status = status;
+  if (res->T || res->Y || res->F) {
+    int rc = device_copy_outputs(p, res);
+    if (rc != MCF_OK) return rc;
+  }
+  return status;
+}
+
+template <typename P, typename S>
+static int copy_outputs_t(mcf_problem* p, DeviceState* d, mcf_result* res, cudaStream_t st) {
+  const int n = d->n, m = d->m;
+  const size_t ld = d->ld;
+  std::vector<P> buf;
+  if (res->T || res->Y) {
+    buf.resize((size_t)n * ld);
+    if (res->T) {
+      CK(cudaMemcpyAsync(buf.data(), d->That, buf.size() * sizeof(P), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) res->T[(size_t)i * n + j] = (double)buf[(size_t)j * ld + i];
+    }
+    if (res->Y) {
+      CK(cudaMemcpyAsync(buf.data(), d->Yhat, buf.size() * sizeof(P), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) res->Y[(size_t)i * n + j] = (double)buf[(size_t)j * ld + i];
+    }
+  }
+  if (res->F) {
+    P* tmp = nullptr;
+    if (cudaMalloc((void**)&tmp, (size_t)m * ld * sizeof(P)) != cudaSuccess) {
+      cudaGetLastError();
+      set_error("device allocation for the F output failed");
+      return MCF_ERR_OOM;
+    }
+    const int prev = d->cur ^ 1;   // F^{k-3/2} and Y^{k-1} of the last iteration
+    fhat_kernel<P, S><<<2048, 256, 0, st>>>((const S*)d->F[prev], (const P*)d->Y[prev], d->e_tail,
+                                           d->e_head, (const P*)d->mu, d->sc, tmp, m, (int)ld);
+    buf.resize((size_t)m * ld);
+    cudaError_t e = cudaMemcpyAsync(buf.data(), tmp, buf.size() * sizeof(P), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(tmp);
+    CK(e);
+    const std::vector<int32_t>& perm = p->topo.perm;
+    for (int e2 = 0; e2 < m; ++e2) {
+      const int l = perm[e2];
+      for (int i = 0; i < n; ++i) res->F[(size_t)i * m + l] = (double)buf[(size_t)e2 * ld + i];
+    }
+  }
+  return MCF_OK;
+}
+
+}  // namespace pdmcf
+
+extern "C" int mcf_shape_info(int* group, int* vpt, int* block) {
+  for (int s = 0; s < pdmcf::NUM_SHAPES; ++s) {
+    if (group) group[s] = pdmcf::kShapes[s].group;
+    if (vpt) vpt[s] = pdmcf::kShapes[s].vpt;
+    if (block) block[s] = pdmcf::kShapes[s].block;
+  }
+  return pdmcf::NUM_SHAPES;
+}
+
+namespace pdmcf {
+
+int device_copy_outputs(mcf_problem* p, mcf_result* res) {
+  DeviceState* d = p->ds;
+  if (!d || !d->valid) {
+    set_error("no solution resident on the device");
+    return MCF_ERR_INVALID;
+  }
+  CK(cudaSetDevice(d->device));
+  cudaStream_t st = d->own_stream;
+  if (d->precision == MCF_FP64) return copy_outputs_t<double, double>(p, d, res, st);
+  if (d->precision == MCF_BF16_F) return copy_outputs_t<float, __nv_bfloat16>(p, d, res, st);
+  return copy_outputs_t<float, float>(p, d, res, st);
+}
+
+int device_solve(mcf_problem* p, const mcf_options* o, mcf_result* res, mcf_kernel_times* kt) {
+  const int prec = o->precision;
+  if (prec != MCF_FP32 && prec != MCF_FP64 && prec != MCF_BF16_F) {
+    set_error("unknown precision");
+    return MCF_ERR_INVALID;
+  }
+  cudaStream_t user = (cudaStream_t)o->cuda_stream;
+  if (p->ds && (p->ds->precision != prec || p->ds->device != o->device)) device_free(p);
+  if (!p->ds) {
+    int rc = alloc_state(p, prec, o->device, o->shape, user, &p->ds);
+    if (rc != MCF_OK) return rc;
+  }
+  DeviceState* d = p->ds;
+  CK(cudaSetDevice(d->device));
+  if (o->shape != d->shape && !(o->shape < 0 && d->shape == d->auto_shape)) {
+    // a different launch shape: new grids and partial arrays, same resident iterate
+    int rc = configure_shape(d, o->shape);
+    if (rc == MCF_OK) rc = alloc_partials(d);
+    if (rc != MCF_OK) return rc;
+    destroy_graphs(d);
+  }
+  cudaStream_t st = user ? user : d->own_stream;
+  if (prec == MCF_FP64) return solve_t<double, double>(p, d, o, res, st, kt);
+  if (prec == MCF_BF16_F) return solve_t<float, __nv_bfloat16>(p, d, o, res, st, kt);
+  return solve_t<float, float>(p, d, o, res, st, kt);
+}
+
+}  // namespace pdmcf

@@ -1,0 +1,45 @@
+"""Write the oracle's converged solutions used as expected values by the GPU parity tests.
+
+Calls only the CPU oracle (oracle/) and the seeded input generators. Each case is solved
+to a relative KKT measure of 1e-9 (or the stated tolerance) in float64; the file stores
+T, Y^, the utility and the final metrics. Run: python tests/golden/make_golden.py [case...]
+"""
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+from oracle import pdmcf as O  # noqa: E402
+from paper_2501_17996_gb300 import instances as I  # noqa: E402
+
+CASES = {
+    # name: (instance factory, rel_kkt tolerance)
+    "tiny_s0": (lambda: I.tiny(0), 1e-10),
+    "mid_s0": (lambda: I.mid(0), 1e-9),
+    "midpow_s0": (lambda: I.large(0, n=100), 1e-9),
+    "slice_s0": (lambda: I.large_slice(0), 1e-7),
+}
+
+
+def make(name: str) -> str:
+    factory, tol = CASES[name]
+    inst = factory()
+    t0 = time.time()
+    r = O.pdmcf(inst.n, inst.tail, inst.head, inst.cap, inst.kind, inst.w, inst.gamma,
+                eps=tol, stop_mode="kkt", max_iters=500000, k_check=10)
+    path = os.path.join(HERE, f"oracle_{name}.npz")
+    np.savez_compressed(path, T=r.T, Yhat=r.Yhat, utility=r.utility, iters=r.iters,
+                        rel_kkt=r.metrics.rel_kkt, rel_gap=r.metrics.rel_gap,
+                        status=r.status, omega=r.omega)
+    print(f"{name}: {r.status} iters={r.iters} rel_kkt={r.metrics.rel_kkt:.3g} "
+          f"U={r.utility:.12g} {time.time() - t0:.1f}s -> {path}", flush=True)
+    return path
+
+
+if __name__ == "__main__":
+    for name in (sys.argv[1:] or ["tiny_s0", "mid_s0", "midpow_s0"]):
+        make(name)

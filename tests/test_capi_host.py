@@ -1,0 +1,117 @@
+"""C ABI checks that need no GPU: the library loads, exports every declared symbol, and
+rejects invalid input with the documented codes before touching a device."""
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2501_17996_gb300 import instances as I
+
+from .conftest import HAS_GPU
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "pdmcf.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mcf_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib.LIB, name), name
+    assert set(names) == set(lib.SYMBOLS)
+
+
+def test_options_defaults_are_the_paper_constants(lib):
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_constants.json")))
+    o = lib.mcf_options_default()
+    assert o.rho == gold["rho"]["value"]
+    assert o.theta == gold["theta"]["value"]
+    assert o.k_adapt == gold["k_adapt"]["value"]
+    assert o.tau == gold["tau"]["value"]
+    assert o.omega0 == gold["omega0"]["value"]
+    assert o.shape == -1 and o.precision == lib.MCF_FP32
+
+
+def _create(lib, n, t, h, c, kind="log", w=None, gamma=None):
+    if w is None:
+        w = np.ones((n, n))
+    return lib.mcf_create_problem(n, t, h, c, kind, w, gamma)
+
+
+@pytest.mark.parametrize("case,code", [
+    ("n1", -1), ("oob", -1), ("selfloop", -1), ("dup", -1), ("cap0", -1), ("capnan", -1),
+    ("w0", -1), ("gamma_missing", -1), ("gamma_range", -1), ("disconnected", -2),
+])
+def test_invalid_problems_are_rejected(lib, case, code):
+    n, t, h, c = 3, [0, 1, 2], [1, 2, 0], [1.0, 1.0, 1.0]
+    kw = {}
+    if case == "n1":
+        n, t, h, c = 1, [0], [0], [1.0]
+    elif case == "oob":
+        h = [1, 2, 3]
+    elif case == "selfloop":
+        h = [0, 2, 0]
+    elif case == "dup":
+        t, h, c = [0, 1, 2, 0], [1, 2, 0, 1], [1.0] * 4
+    elif case == "cap0":
+        c = [1.0, 0.0, 1.0]
+    elif case == "capnan":
+        c = [1.0, float("nan"), 1.0]
+    elif case == "w0":
+        w = np.ones((3, 3))
+        w[1, 2] = 0.0
+        kw["w"] = w
+    elif case == "gamma_missing":
+        kw["kind"] = "pow"
+    elif case == "gamma_range":
+        kw["kind"] = "pow"
+        kw["gamma"] = 1.5
+    elif case == "disconnected":
+        t, h, c = [0, 1], [1, 0], [1.0, 1.0]
+    with pytest.raises(lib.MCFError) as ei:
+        _create(lib, n, t, h, c, **kw)
+    assert ei.value.code == code
+    assert lib.mcf_last_error() != ""
+
+
+def test_valid_problem_and_footprint(lib):
+    inst = I.mid(0)
+    with lib.Problem(inst) as p:
+        b32 = p.device_bytes("fp32")
+        b16 = p.device_bytes("bf16")
+        b64 = p.device_bytes("fp64")
+        ld = 104
+        assert b32 >= 2 * inst.m * ld * 4 + 2 * inst.n * ld * 4
+        assert b16 < b32 < b64
+
+
+def test_invalid_options_are_rejected(lib):
+    with lib.Problem(I.tiny(0)) as p:
+        for bad in [dict(rho=2.0), dict(rho=0.0), dict(k_check=0), dict(max_iters=0),
+                    dict(eps=0.0), dict(precision=7), dict(shape=99), dict(theta=1.5)]:
+            with pytest.raises(lib.MCFError) as ei:
+                p.solve(**bad)
+            assert ei.value.code == lib.MCF_ERR_INVALID, bad
+
+
+@pytest.mark.skipif(HAS_GPU, reason="checks the behaviour on a machine without a GPU")
+def test_solve_without_gpu_fails_loudly(lib):
+    with lib.Problem(I.tiny(0)) as p:
+        with pytest.raises(lib.MCFError) as ei:
+            p.solve()
+        assert ei.value.code == lib.MCF_ERR_CUDA
+    assert "no CUDA device" in lib.mcf_last_error() or "CUDA" in lib.mcf_last_error()
+
+
+def test_shape_table(lib):
+    shapes = lib.mcf_shape_info()
+    assert len(shapes) >= 10
+    for g, v, b in shapes:
+        assert g in (32, 64, 128, 256, 512, 1024) and b % g == 0 and v >= 1

@@ -1,0 +1,254 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+  * trajectory parity: both run exactly K iterations of Algorithm 2.1 from the same cold
+    start; T = -F^A^T, Y^ and F^ of iteration K are compared element by element (FP64 path:
+    1e-8 of scale; FP32 path: 1e-4 of scale), for every kernel launch shape;
+  * converged parity (the acceptance criterion): the FP32 solve stopped at relative KKT
+    1e-4 against the oracle run to 1e-9: relative utility error <= 1e-4 and max relative
+    error of the off-diagonal T <= 1e-3;
+  * closed forms (two nodes, first iteration), warm-start continuation, determinism,
+    graphs vs plain launches, async vs sync;
+  * properties at full size (n = 10^4, m = 10^5, the benchmark's launch shape).
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import pdmcf as O
+from paper_2501_17996_gb300 import instances as I
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def off(n):
+    return ~np.eye(n, dtype=bool)
+
+
+def oracle_k(inst, K):
+    return O.pdmcf(inst.n, inst.tail, inst.head, inst.cap, inst.kind, inst.w, inst.gamma,
+                   stop_mode="none", max_iters=K)
+
+
+def rel_err(a, b, mask=None):
+    if mask is not None:
+        a, b = a[mask], b[mask]
+    scale = max(np.abs(b).max(), 1e-300)
+    return float(np.abs(a - b).max() / scale)
+
+
+def shapes_for(lib, inst, precision):
+    vw = {"fp32": 4, "fp64": 2, "bf16": 8}[precision]
+    nchunks = ((inst.n + 7) // 8 * 8) // vw
+    out = []
+    for s, (g, v, b) in enumerate(lib.mcf_shape_info()):
+        if g * v >= nchunks and not (precision == "fp64" and s >= 10):
+            out.append(s)
+    return out
+
+
+# ------------------------------------------------------------------ trajectory parity
+
+TRAJ_CASES = {
+    "tiny": lambda: I.tiny(0),
+    "mid": lambda: I.mid(0),
+    "midpow": lambda: I.large(0, n=100),
+    "two_node": lambda: I.two_node(1.7, 0.45),
+    "pairgamma": lambda: _pair_gamma(),
+}
+
+
+def _pair_gamma():
+    inst = I.random_small(9, 30, 5, kind="pow")
+    rng = np.random.default_rng(3)
+    inst.gamma = rng.uniform(0.3, 0.7, size=(inst.n, inst.n))
+    return inst
+
+
+@pytest.mark.parametrize("case", list(TRAJ_CASES))
+def test_fp64_trajectory_matches_oracle(lib, case):
+    inst = TRAJ_CASES[case]()
+    K = 200
+    ref = oracle_k(inst, K)
+    with lib.Problem(inst) as p:
+        g = p.solve(precision="fp64", stop_mode="none", max_iters=K, k_check=25,
+                    want_T=True, want_F=True, want_Y=True)
+    m = off(inst.n)
+    assert g["iters"] == K
+    assert rel_err(g["T"], ref.T, m) < 1e-8
+    assert rel_err(g["Y"], ref.Yhat, m) < 1e-8
+    assert rel_err(g["F"], ref.Fhat) < 1e-8
+    assert g["omega"] == pytest.approx(ref.omega, rel=1e-8)
+    assert np.all(np.diag(g["Y"]) == 0)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_every_shape_matches_oracle(lib, precision):
+    inst = I.mid(0) if precision == "fp32" else I.tiny(0)
+    K = 30
+    ref = oracle_k(inst, K)
+    m = off(inst.n)
+    tol = 1e-4 if precision == "fp32" else 1e-9
+    shapes = shapes_for(lib, inst, precision)
+    assert len(shapes) >= 10
+    with lib.Problem(inst) as p:
+        for s in shapes:
+            g = p.solve(precision=precision, stop_mode="none", max_iters=K, k_check=10,
+                        shape=s, want_T=True, want_F=True, want_Y=True)
+            assert rel_err(g["T"], ref.T, m) < tol, s
+            assert rel_err(g["Y"], ref.Yhat, m) < tol, s
+            assert rel_err(g["F"], ref.Fhat) < tol, s
+
+
+def test_slice_trajectory_fp32(lib):
+    """The large recipe (power utility, gamma = 1/2, lognormal capacities) at n = 1000."""
+    inst = I.large_slice(0)
+    K = 12
+    ref = oracle_k(inst, K)
+    with lib.Problem(inst) as p:
+        g = p.solve(precision="fp32", stop_mode="none", max_iters=K, k_check=4,
+                    want_T=True, want_Y=True)
+    m = off(inst.n)
+    assert rel_err(g["T"], ref.T, m) < 1e-4
+    assert rel_err(g["Y"], ref.Yhat, m) < 1e-4
+
+
+# ------------------------------------------------------------------ converged parity
+
+@pytest.mark.parametrize("name,precision,tol", [("tiny_s0", "fp64", 1e-6),
+                                                ("mid_s0", "fp32", 1e-4),
+                                                ("midpow_s0", "fp32", 1e-4)])
+def test_converged_matches_oracle(lib, name, precision, tol):
+    gold = np.load(os.path.join(GOLDEN, f"oracle_{name}.npz"))
+    inst = {"tiny_s0": lambda: I.tiny(0), "mid_s0": lambda: I.mid(0),
+            "midpow_s0": lambda: I.large(0, n=100)}[name]()
+    with lib.Problem(inst) as p:
+        g = p.solve(precision=precision, stop_mode="kkt", eps=tol, max_iters=200000,
+                    k_check=50, want_T=True, want_Y=True)
+    assert g["rc"] == lib.MCF_OK and g["rel_kkt"] < tol
+    m = off(inst.n)
+    Tstar = gold["T"]
+    assert abs(g["utility"] - float(gold["utility"])) <= 1e-4 * abs(float(gold["utility"]))
+    assert np.max(np.abs(g["T"][m] - Tstar[m]) / Tstar[m]) <= 1e-3
+    assert np.allclose(g["T"].sum(axis=1), 0, atol=1e-4 * np.abs(Tstar).max())
+    assert g["feasible"] == 1 and g["rel_gap"] >= -1e-6
+    assert g["utility"] <= g["dual_bound"] + 1e-6 * abs(g["dual_bound"])
+
+
+# ------------------------------------------------------------------ closed forms and edges
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_two_node_closed_form(lib, precision):
+    ca, cb = 1.7, 0.45
+    inst = I.two_node(ca, cb, "log", w12=0.8, w21=1.3)
+    with lib.Problem(inst) as p:
+        g = p.solve(precision=precision, stop_mode="kkt", eps=1e-6, max_iters=20000,
+                    want_T=True, want_Y=True)
+    tol = 1e-5 if precision == "fp32" else 1e-9
+    assert g["T"][1, 0] == pytest.approx(ca, rel=tol)
+    assert g["T"][0, 1] == pytest.approx(cb, rel=tol)
+    assert g["Y"][1, 0] == pytest.approx(-1.3 / ca, rel=10 * tol)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_first_iteration_closed_form(lib, precision):
+    """From the cold start, F^{1/2} = alpha e_head per edge (alpha <= c_l), hence
+    T_ij = alpha if the edge j -> i exists, 0 otherwise, T_ii = -alpha indeg(i)."""
+    inst = I.mid(1)
+    alpha = O.eta_bound(inst.n, inst.tail, inst.head)
+    assert np.all(alpha <= inst.cap)
+    Tref = np.zeros((inst.n, inst.n))
+    Tref[inst.head, inst.tail] = alpha
+    np.fill_diagonal(Tref, -alpha * np.bincount(inst.head, minlength=inst.n))
+    with lib.Problem(inst) as p:
+        g = p.solve(precision=precision, stop_mode="none", max_iters=1, want_T=True)
+    tol = 1e-6 if precision == "fp32" else 1e-14
+    assert np.abs(g["T"] - Tref).max() <= tol * alpha * 20
+    assert g["feasible"] == 0 and g["nonpos_frac"] > 0
+
+
+def test_warm_start_continues_the_iteration(lib):
+    """Solving 100 iterations and then 60 warm-started ones equals 160 cold iterations
+    (k restarts at 0 on a warm start, and 100 is a multiple of k_adapt)."""
+    inst = I.mid(0)
+    with lib.Problem(inst) as p:
+        a = p.solve(precision="fp64", stop_mode="none", max_iters=160, want_T=True, want_Y=True)
+        p.solve(precision="fp64", stop_mode="none", max_iters=100)
+        b = p.solve(precision="fp64", stop_mode="none", max_iters=60, warm_start=1,
+                    want_T=True, want_Y=True)
+    assert np.array_equal(a["T"], b["T"])
+    assert np.array_equal(a["Y"], b["Y"])
+
+
+def test_deterministic_and_graphs_equal_plain_launches(lib):
+    inst = I.mid(2)
+    with lib.Problem(inst) as p:
+        r1 = p.solve(stop_mode="none", max_iters=150, k_check=50, want_T=True, want_Y=True)
+        r2 = p.solve(stop_mode="none", max_iters=150, k_check=50, want_T=True, want_Y=True)
+        r3 = p.solve(stop_mode="none", max_iters=150, k_check=50, use_graphs=0,
+                     want_T=True, want_Y=True)
+    for key in ("T", "Y"):
+        assert np.array_equal(r1[key], r2[key])
+        assert np.array_equal(r1[key], r3[key])
+    assert r1["rel_kkt"] == r2["rel_kkt"] == r3["rel_kkt"]
+
+
+def test_async_matches_sync(lib):
+    insts = [I.mid(s) for s in range(3)] + [I.tiny(1)]
+    sync = []
+    for inst in insts:
+        with lib.Problem(inst) as p:
+            sync.append(p.solve(stop_mode="kkt", eps=1e-4, want_T=True))
+    probs = [lib.Problem(inst) for inst in insts]
+    tickets = [p.submit(stop_mode="kkt", eps=1e-4) for p in probs]
+    for t, p, s in zip(tickets, probs, sync):
+        r = lib.mcf_wait(t, 120000, p.n, p.m, want_T=True)
+        assert r is not None and r["status"] == lib.MCF_OK
+        assert r["iters"] == s["iters"]
+        assert np.array_equal(r["T"], s["T"])
+    for p in probs:
+        p.close()
+
+
+def test_capacity_update_warm_resolve(lib):
+    inst = I.mid(3)
+    rng = np.random.default_rng(0)
+    pert = I.perturb(inst, 0.1, "cap", rng)
+    ref = O.pdmcf(pert.n, pert.tail, pert.head, pert.cap, pert.kind, pert.w, eps=1e-8,
+                  stop_mode="kkt", max_iters=100000, k_check=10)
+    with lib.Problem(inst) as p:
+        cold = p.solve(stop_mode="kkt", eps=1e-4)
+        p.update_capacities(pert.cap)
+        warm = p.solve(stop_mode="kkt", eps=1e-4, warm_start=1, want_T=True)
+    assert warm["rc"] == lib.MCF_OK
+    assert abs(warm["utility"] - ref.utility) <= 1e-4 * abs(ref.utility)
+    assert cold["iters"] > 0
+
+
+# ------------------------------------------------------------------ full size
+
+def test_large_properties_at_full_size(lib):
+    """n = 10^4, m = 10^5 (power utility, gamma = 1/2) in the benchmark's launch shape:
+    the first-iteration closed form, then certificates after 300 iterations."""
+    inst = I.large(0)
+    n = inst.n
+    alpha = O.eta_bound(n, inst.tail, inst.head)
+    rows = np.random.default_rng(0).choice(n, size=64, replace=False)
+    with lib.Problem(inst) as p:
+        g = p.solve(stop_mode="none", max_iters=1, want_T=True)
+        T = g["T"]
+        for i in rows:
+            ref = np.zeros(n)
+            ref[inst.tail[inst.head == i]] = alpha
+            ref[i] = -alpha * np.sum(inst.head == i)
+            assert np.abs(T[i] - ref).max() <= 1e-6 * alpha * 40
+        g = p.solve(stop_mode="none", max_iters=300, k_check=100, want_T=True, want_Y=True)
+    T, Y = g["T"], g["Y"]
+    assert np.all(np.diag(Y) == 0)
+    assert np.all(Y[off(n)] < 0)
+    assert np.abs(T[rows].sum(axis=1)).max() <= 1e-4 * np.abs(T[rows]).max()
+    if g["feasible"]:
+        assert g["utility"] <= g["dual_bound"] * (1 + 1e-6)
+    assert np.isfinite(g["rel_cons"])
