@@ -47,6 +47,12 @@ WORKLOADS = {
     "large": dict(factory=lambda seed: I.large(seed), sample=lambda seed: I.large_slice(seed),
                   desc="n=10000, m=100000 (ring + 9 random out-edges per node), "
                        "c~lognormal(0,0.5), u = w s^0.5, w~U[0.5,1.5]"),
+    # profiling case: the large per-edge vector length (n = 10^4, same kernel shape) with
+    # out-degree 2, so one capture holds ~4 GB on the device
+    "prof": dict(factory=lambda seed: I.ring_random_instance(10000, 2, seed, "lognormal", "pow",
+                                                             gamma=0.5, name="prof"),
+                 sample=lambda seed: I.large_slice(seed),
+                 desc="n=10000, m=20000 (ring + 1 random out-edge per node), large recipe"),
     "mid": dict(factory=lambda seed: I.mid(seed), sample=lambda seed: I.mid(seed),
                 desc="n=100, m=1000 (ring + 9 random out-edges per node), c~U[1,10], "
                      "u = w log s, w~U[0.5,1.5]"),
@@ -185,7 +191,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     wl = WORKLOADS[args.workload]
-    inst_n, inst_m = (10000, 100000) if args.workload == "large" else (100, 1000)
+    inst_n, inst_m = {"large": (10000, 100000), "prof": (10000, 20000), "mid": (100, 1000)}[args.workload]
     sample = wl["sample"](args.seed)
     if args.workload == "large" and args.steps + args.warmup > 60:
         sample = I.large(args.seed, n=500)
@@ -273,16 +279,18 @@ def run_ours(args, rank, world, local_rank):
     prob.close()
 
     # ---- end to end through the public API with host buffers
-    torch.cuda.synchronize()
-    barrier()
-    t0 = time.perf_counter()
-    with B.Problem(inst) as p2:
-        r2 = p2.solve(want_T=True, max_iters=args.steps, **common)
-    t_e2e = time.perf_counter() - t0
-    tt = torch.tensor([t_e2e], device="cuda")
-    if world > 1:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    e2e_value = world * args.steps / float(tt.item())
+    e2e_value = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        with B.Problem(inst) as p2:
+            p2.solve(want_T=True, max_iters=args.steps, **common)
+        t_e2e = time.perf_counter() - t0
+        tt = torch.tensor([t_e2e], device="cuda")
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_value = world * args.steps / float(tt.item())
     ld = (n + 7) // 8 * 8
     h2d = (n * ld * s_p) + m * s_p + (3 * m + 2 * (n + 1)) * 4     # W, cap, incidence
     d2h = n * ld * s_p                                             # T
@@ -344,6 +352,7 @@ def main():
     ap.add_argument("--ttt-eps", dest="ttt_eps", type=float, default=1e-4)
     ap.add_argument("--ttt-max-iters", dest="ttt_max_iters", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
+    ap.add_argument("--no-e2e", dest="no_e2e", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
