@@ -196,6 +196,31 @@ typedef struct mcf_kernel_times {
 int mcf_solve_timed(mcf_problem* p, const mcf_options* opts, mcf_result* res,
                     mcf_kernel_times* kt);
 
+/* ---------------------------------------------------------------- operators on device arrays */
+
+/* The projection Pi onto the feasible flow set of Sec. 2.3, one column at a time: for each
+ * of the m columns q_l (row l of Qt), Ft row l = (q_l - mu_l 1)_+ where mu_l = 0 if
+ * sum_i (q_il)_+ <= cap_l, else the unique mu_l > 0 with sum_i (q_il - mu_l)_+ = cap_l
+ * (the value the sorted scan of Sec. 2.6 gives).
+ *   n      column length (number of destinations), 1 <= n <= 32768
+ *   m      number of columns (>= 0)
+ *   ld     row stride of Qt and Ft in floats: ld >= n, ld % 4 == 0
+ *   Qt     device, m x ld floats, 16-byte aligned; entries n..ld-1 of each row are ignored
+ *   cap    device, m capacities > 0
+ *   Ft     device, m x ld floats, 16-byte aligned; entries n..ld-1 are written as 0. Ft may
+ *          equal Qt (in place)
+ *   mu     device, m floats: on entry a starting guess (0 = none; any value >= 0 is valid),
+ *          on exit the multipliers mu_l
+ *   dist2  host, may be NULL: receives sum_l ||Ft_l - q_l||^2, an FP64 reduction in a fixed
+ *          order (independent of the launch grid)
+ *   stream cudaStream_t (NULL = legacy default stream), on the calling thread's current device
+ * Allocates m+1 doubles of device scratch for the call and synchronizes the stream before
+ * returning. Errors: MCF_ERR_INVALID (sizes, NULL or misaligned pointers), MCF_ERR_OOM,
+ * MCF_ERR_CUDA. */
+int mcf_project_capped_simplex(int32_t n, int32_t m, int32_t ld, const float* Qt,
+                               const float* cap, float* Ft, float* mu, double* dist2,
+                               void* stream);
+
 /* Launch shape table: shape s gives `group` threads per edge/node, each holding `vpt`
  * 16-byte chunks of the edge/node vector (capacity group*vpt chunks of 16 bytes of F).
  * Returns the number of shapes; fills the three arrays (may be NULL) up to that count. */

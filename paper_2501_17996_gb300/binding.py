@@ -66,7 +66,8 @@ SYMBOLS = [
     "mcf_create_problem", "mcf_update_capacities", "mcf_update_weights",
     "mcf_destroy_problem", "mcf_problem_size", "mcf_problem_device_bytes",
     "mcf_options_default", "mcf_solve", "mcf_solve_timed", "mcf_submit", "mcf_poll", "mcf_wait",
-    "mcf_cancel", "mcf_serving_config", "mcf_shape_info", "mcf_last_error", "mcf_version",
+    "mcf_cancel", "mcf_serving_config", "mcf_project_capped_simplex", "mcf_shape_info",
+    "mcf_last_error", "mcf_version",
 ]
 
 
@@ -96,6 +97,8 @@ def _load() -> C.CDLL:
         "mcf_wait": (C.c_int, [C.c_int64, C.c_int64, C.POINTER(C.c_int), C.POINTER(mcf_result)]),
         "mcf_cancel": (C.c_int, [C.c_int64]),
         "mcf_serving_config": (C.c_int, [C.c_int64, C.c_int]),
+        "mcf_project_capped_simplex": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P, P, P,
+                                                 dp, P]),
         "mcf_shape_info": (C.c_int, [ip, ip, ip]),
         "mcf_last_error": (C.c_char_p, []),
         "mcf_version": (C.c_char_p, []),
@@ -283,6 +286,17 @@ def mcf_cancel(ticket: int) -> None:
     rc = LIB.mcf_cancel(ticket)
     if rc != MCF_OK:
         raise MCFError(rc, "mcf_cancel")
+
+
+def mcf_project_capped_simplex(n: int, m: int, ld: int, Qt_ptr: int, cap_ptr: int, Ft_ptr: int,
+                               mu_ptr: int, stream: int = 0) -> float:
+    """Device pointers (ints, e.g. torch tensor.data_ptr()); returns sum ||F - Q||^2."""
+    d2 = C.c_double(0.0)
+    rc = LIB.mcf_project_capped_simplex(int(n), int(m), int(ld), Qt_ptr, cap_ptr, Ft_ptr, mu_ptr,
+                                        C.byref(d2), stream or None)
+    if rc != MCF_OK:
+        raise MCFError(rc, "mcf_project_capped_simplex")
+    return d2.value
 
 
 def mcf_serving_config(hbm_budget_bytes: int, max_resident: int) -> None:

@@ -121,6 +121,18 @@ template <int GROUP> struct GroupScratch {
   double x[2][NW];
 };
 
+// Cross-warp stage of a block-wide group reduction: lane l < NW of every warp loads warp
+// l's partial and a butterfly over NW lanes finishes it. Every warp evaluates the same
+// tree on the same values, so all threads agree bit for bit. NW is a power of two.
+template <int NW, typename T, typename Op>
+__device__ __forceinline__ T cross_warp(T mine_if_lane_lt_nw, T ident, Op op) {
+  T v = mine_if_lane_lt_nw;
+#pragma unroll
+  for (int o = NW / 2; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+  (void)ident;
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+
 template <int GROUP, typename P>
 __device__ __forceinline__ void group_sum_count(P& s, int& c, GroupScratch<GROUP>& sh, int& phase) {
 #pragma unroll
@@ -133,10 +145,10 @@ __device__ __forceinline__ void group_sum_count(P& s, int& c, GroupScratch<GROUP
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) { sh.s[phase][warp] = (double)s; sh.c[phase][warp] = c; }
     __syncthreads();
-    P ts = 0; int tc = 0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) { ts += (P)sh.s[phase][w]; tc += sh.c[phase][w]; }
-    s = ts; c = tc;
+    P ps = lane < NW ? (P)sh.s[phase][lane] : P(0);
+    int pc = lane < NW ? sh.c[phase][lane] : 0;
+    s = cross_warp<NW>(ps, P(0), [](P a, P b) { return a + b; });
+    c = cross_warp<NW>(pc, 0, [](int a, int b) { return a + b; });
     phase ^= 1;
   }
 }
@@ -150,10 +162,25 @@ __device__ __forceinline__ P group_max(P v, GroupScratch<GROUP>& sh, int& phase)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) sh.x[phase][warp] = (double)v;
     __syncthreads();
-    P t = (P)sh.x[phase][0];
+    P pv = lane < NW ? (P)sh.x[phase][lane] : (P)(-INFINITY);
+    v = cross_warp<NW>(pv, (P)(-INFINITY), [](P a, P b) { return fmax(a, b); });
+    phase ^= 1;
+  }
+  return v;
+}
+
+// Group-wide sum of one double (same value in every thread of the group).
+template <int GROUP>
+__device__ __forceinline__ double group_sum_double(double v, GroupScratch<GROUP>& sh, int& phase) {
 #pragma unroll
-    for (int w = 1; w < NW; ++w) t = fmax(t, (P)sh.x[phase][w]);
-    v = t;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if constexpr (GROUP > 32) {
+    constexpr int NW = GROUP / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sh.x[phase][warp] = v;
+    __syncthreads();
+    double pv = lane < NW ? sh.x[phase][lane] : 0.0;
+    v = cross_warp<NW>(pv, 0.0, [](double a, double b) { return a + b; });
     phase ^= 1;
   }
   return v;
@@ -383,6 +410,7 @@ edge_kernel(IterArgs<P, S> a) {
       }
     }
     const P mu = project_mu<GROUP, VPT, VW, P>(q, c, mu0, sh, phase);
+    P dloc = P(0);   // this thread's part of ||dF||^2 for this edge; FP64 across edges
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
       const int ci = v * GROUP + lane;
@@ -393,12 +421,13 @@ edge_kernel(IterArgs<P, S> a) {
           const P fh = q[v][u] > mu ? q[v][u] - mu : P(0);
           const P fnew = rho * fh + (P(1) - rho) * f[v][u];
           out[u] = from_p<S, P>(fnew);
-          const double d = (double)(to_p<P>(out[u]) - f[v][u]);
-          dsum += d * d;
+          const P d = to_p<P>(out[u]) - f[v][u];
+          dloc = fma(d, d, dloc);
         }
         st_stream<S, VW>(Fn + (size_t)e * a.ld + ci * VW, out);
       }
     }
+    dsum += (double)dloc;
     if (lane == 0) a.mu[e] = mu;
   }
   double v1[1] = {dsum};
@@ -434,34 +463,47 @@ node_kernel(IterArgs<P, S> a) {
     for (int v = 0; v < VPT; ++v)
 #pragma unroll
       for (int u = 0; u < VW; ++u) s[v][u] = P(0);
-    const int ib = a.in_ptr[j], ie = a.in_ptr[j + 1];
-    for (int e = ib; e < ie; ++e) {
-      const S* fr = Fn + (size_t)e * a.ld;
+    // p_j = sum_{in(j)} f_new - sum_{out(j)} f_new, two edge rows in flight per step
+    const int ib = a.in_ptr[j], nin = a.in_ptr[j + 1] - ib;
+    const int ob = a.out_ptr[j], deg = nin + (a.out_ptr[j + 1] - ob);
+    auto row = [&](int k) -> const S* {
+      return Fn + (size_t)(k < nin ? ib + k : a.out_idx[ob + k - nin]) * a.ld;
+    };
+    int k = 0;
+    for (; k + 1 < deg; k += 2) {
+      const S* r0 = row(k);
+      const S* r1 = row(k + 1);
+      const P s0 = k < nin ? P(1) : P(-1);
+      const P s1 = k + 1 < nin ? P(1) : P(-1);
 #pragma unroll
       for (int v = 0; v < VPT; ++v) {
         const int ci = v * GROUP + lane;
         if (ci < nchunks) {
-          S fs[VW];
-          ld_plain<S, VW>(fr + ci * VW, fs);
+          S f0[VW], f1[VW];
+          ld_plain<S, VW>(r0 + ci * VW, f0);
+          ld_plain<S, VW>(r1 + ci * VW, f1);
 #pragma unroll
-          for (int u = 0; u < VW; ++u) s[v][u] += to_p<P>(fs[u]);
+          for (int u = 0; u < VW; ++u) s[v][u] += s0 * to_p<P>(f0[u]) + s1 * to_p<P>(f1[u]);
         }
       }
     }
-    const int ob = a.out_ptr[j], oe = a.out_ptr[j + 1];
-    for (int k = ob; k < oe; ++k) {
-      const S* fr = Fn + (size_t)a.out_idx[k] * a.ld;
+    if (k < deg) {
+      const S* r0 = row(k);
+      const P s0 = k < nin ? P(1) : P(-1);
 #pragma unroll
       for (int v = 0; v < VPT; ++v) {
         const int ci = v * GROUP + lane;
         if (ci < nchunks) {
-          S fs[VW];
-          ld_plain<S, VW>(fr + ci * VW, fs);
+          S f0[VW];
+          ld_plain<S, VW>(r0 + ci * VW, f0);
 #pragma unroll
-          for (int u = 0; u < VW; ++u) s[v][u] -= to_p<P>(fs[u]);
+          for (int u = 0; u < VW; ++u) s[v][u] += s0 * to_p<P>(f0[u]);
         }
       }
     }
+    P loc[NODE_PARTS];
+#pragma unroll
+    for (int k = 0; k < NODE_PARTS; ++k) loc[k] = P(0);
     P* prow = a.Pm + (size_t)j * a.ld;
     const P* yrow = Yo + (size_t)j * a.ld;
     const P* wrow = a.W + (size_t)j * a.ld;
@@ -492,26 +534,26 @@ node_kernel(IterArgs<P, S> a) {
           yhat = a.kind == 0 ? prox_log<P>(vv, beta, wv[u]) : prox_pow<P>(vv, beta, wv[u], gv[u]);
         }
         yn[u] = rho * yhat + (P(1) - rho) * yo[u];
-        const double dy = (double)(yn[u] - yo[u]);
-        acc[0] += dy * dy;
+        const P dy = yn[u] - yo[u];
+        loc[0] = fma(dy, dy, loc[0]);
         const P th = -fhat_at;
         that_v[u] = i < a.n ? th : P(0);
         yh_v[u] = yhat;
         up_v[u] = P(0);
         if (a.check && live) {
-          if (!(th > P(0))) acc[1] += 1.0;
+          if (!(th > P(0))) loc[1] += P(1);
           else {
-            acc[2] += (double)util_value<P>(a.kind, th, wv[u], gv[u]);
+            loc[2] += util_value<P>(a.kind, th, wv[u], gv[u]);
             up_v[u] = util_grad<P>(a.kind, th, wv[u], gv[u]);
           }
           if (yhat < P(0)) {
-            acc[3] += (double)util_conj_neg<P>(a.kind, yhat, wv[u], gv[u]);
-            const double dt = (double)util_traffic<P>(a.kind, yhat, wv[u], gv[u]) - (double)th;
-            acc[4] += dt * dt;
+            loc[3] += util_conj_neg<P>(a.kind, yhat, wv[u], gv[u]);
+            const P dt = util_traffic<P>(a.kind, yhat, wv[u], gv[u]) - th;
+            loc[4] = fma(dt, dt, loc[4]);
           } else {
-            acc[6] += 1.0;
+            loc[6] += P(1);
           }
-          acc[5] += (double)th * (double)th;
+          loc[5] = fma(th, th, loc[5]);
         }
       }
       st_plain<P, VW>(Yn + (size_t)j * a.ld + ci * VW, yn);
@@ -522,6 +564,8 @@ node_kernel(IterArgs<P, S> a) {
         st_plain<P, VW>(a.Yhat + (size_t)j * a.ld + ci * VW, yh_v);
       }
     }
+#pragma unroll
+    for (int k = 0; k < NODE_PARTS; ++k) acc[k] += (double)loc[k];
   }
   block_sum_write<BLOCK, NODE_PARTS>(acc, a.part_node + (size_t)blockIdx.x * NODE_PARTS);
 }
@@ -551,6 +595,7 @@ check_kernel(IterArgs<P, S> a) {
     const P mu = a.mu[e];
     const size_t fo = (size_t)e * a.ld, ho = (size_t)h * a.ld, to = (size_t)t * a.ld;
     P ymax = -INFINITY;
+    P lg2 = P(0), lgd = P(0), ld2 = P(0);
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
       const int ci = v * GROUP + lane;
@@ -570,18 +615,88 @@ check_kernel(IterArgs<P, S> a) {
         if (i >= a.n) continue;
         const P q = to_p<P>(fs[u]) + alpha * (y1[u] - y2[u]);
         const P fh = q > mu ? q - mu : P(0);
-        const double d = (double)fh - (double)q;
-        const double g = (double)g1[u] - (double)g2[u];
-        acc[0] += g * g;
-        acc[1] += g * d;
-        acc[2] += d * d;
+        const P d = fh - q;
+        const P g = g1[u] - g2[u];
+        lg2 = fma(g, g, lg2);
+        lgd = fma(g, d, lgd);
+        ld2 = fma(d, d, ld2);
         ymax = fmax(ymax, z1[u] - z2[u]);
       }
     }
+    acc[0] += (double)lg2;
+    acc[1] += (double)lgd;
+    acc[2] += (double)ld2;
     ymax = group_max<GROUP, P>(ymax, sh, phase);
     if (lane == 0 && ymax > P(0)) acc[3] += (double)a.cap[e] * (double)ymax;
   }
   block_sum_write<BLOCK, CHECK_PARTS>(acc, a.part_check + (size_t)blockIdx.x * CHECK_PARTS);
+}
+
+// ------------------------------------------------------------------ standalone projection
+// Pi of Sec. 2.3 applied to m columns given as rows of Qt (edge-major, ld >= n floats per
+// row): Ft row l = (q_l - mu_l)_+, mu in/out (warm start in, multipliers out), and the
+// per-column FP64 squared distance ||Pi(q_l) - q_l||^2 into col_d2[l]. Entries n..ld-1 of
+// Qt are ignored; those of Ft are written as zero.
+struct ProjArgs {
+  int n, m, ld;
+  const float* Qt;
+  const float* cap;
+  float* Ft;
+  float* mu;
+  double* col_d2;
+};
+
+template <int VPT, int GROUP, int BLOCK, int MINB>
+__global__ void __launch_bounds__(BLOCK, MINB)
+project_kernel(ProjArgs a) {
+  constexpr int VW = 4;
+  constexpr int GPB = BLOCK / GROUP;
+  __shared__ GroupScratch<GROUP> sh_all[GPB];
+  GroupScratch<GROUP>& sh = sh_all[threadIdx.x / GROUP];
+  int phase = 0;
+  const int lane = threadIdx.x % GROUP;
+  const int gid = blockIdx.x * GPB + threadIdx.x / GROUP;
+  const int ngroups = gridDim.x * GPB;
+  const int nchunks = a.ld / VW;
+  for (int e = gid; e < a.m; e += ngroups) {
+    const float* qr = a.Qt + (size_t)e * a.ld;
+    float q[VPT][VW];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      const int ci = v * GROUP + lane;
+      if (ci < nchunks) {
+        ld_stream<float, VW>(qr + ci * VW, q[v]);
+#pragma unroll
+        for (int u = 0; u < VW; ++u)
+          if (ci * VW + u >= a.n) q[v][u] = 0.f;       // pads never enter the active set
+      } else {
+#pragma unroll
+        for (int u = 0; u < VW; ++u) q[v][u] = 0.f;
+      }
+    }
+    const float mu0 = a.mu[e];
+    const float mu = project_mu<GROUP, VPT, VW, float>(q, a.cap[e], mu0 > 0.f ? mu0 : 0.f, sh, phase);
+    float dloc = 0.f;
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      const int ci = v * GROUP + lane;
+      if (ci < nchunks) {
+        float out[VW];
+#pragma unroll
+        for (int u = 0; u < VW; ++u) {
+          out[u] = q[v][u] > mu ? q[v][u] - mu : 0.f;
+          const float d = out[u] - q[v][u];
+          dloc = fmaf(d, d, dloc);
+        }
+        st_stream<float, VW>(a.Ft + (size_t)e * a.ld + ci * VW, out);
+      }
+    }
+    const double d2 = group_sum_double<GROUP>((double)dloc, sh, phase);
+    if (lane == 0) {
+      a.mu[e] = mu;
+      a.col_d2[e] = d2;
+    }
+  }
 }
 
 }  // namespace pdmcf

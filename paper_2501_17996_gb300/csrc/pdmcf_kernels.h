@@ -51,13 +51,22 @@ constexpr int min_blocks() {
                                            : (512 / BLOCK > 0 ? 512 / BLOCK : 1);
 }
 
+// The node phase keeps an accumulator and two gathered rows per chunk: half the residency
+// once those exceed 48 bytes per chunk slot.
+template <typename P, int VPT, int VW, int BLOCK>
+constexpr int min_blocks_node() {
+  return (VPT * VW * (int)sizeof(P) <= 48) ? (1024 / BLOCK > 0 ? 1024 / BLOCK : 1)
+                                           : (512 / BLOCK > 0 ? 512 / BLOCK : 1);
+}
+
 namespace pdmcf {
 template <typename P, typename S, int IDX>
 void fill_shape(KernelTable<P, S>& t) {
   constexpr ShapeDesc d = kShapes[IDX];
   constexpr int MB = min_blocks<P, d.vpt, StoreTraits<S>::VW, d.block>();
   t.edge[IDX] = edge_kernel<P, S, d.vpt, d.group, d.block, MB>;
-  t.node[IDX] = node_kernel<P, S, d.vpt, d.group, d.block, MB>;
+  constexpr int MBN = min_blocks_node<P, d.vpt, StoreTraits<S>::VW, d.block>();
+  t.node[IDX] = node_kernel<P, S, d.vpt, d.group, d.block, MBN>;
   t.check[IDX] = check_kernel<P, S, d.vpt, d.group, d.block, MB>;
 }
 
