@@ -221,6 +221,25 @@ int mcf_project_capped_simplex(int32_t n, int32_t m, int32_t ld, const float* Qt
                                const float* cap, float* Ft, float* mu, double* dist2,
                                void* stream);
 
+/* The same projection for callers that cannot allocate device memory: code running while
+ * a CUDA graph is being captured, processes whose device memory belongs to their own pool
+ * or to a framework allocator, and loops that must never enter the allocator. The paper has
+ * no counterpart; this is a library service. Arguments and results are those of
+ * mcf_project_capped_simplex, except:
+ *   - no device memory is allocated or freed: the scratch (m + 1 doubles) is a fixed array in
+ *     the library image, present on every GPU that loads the library until the process
+ *     exits; m is limited to 262144 columns (MCF_ERR_INVALID beyond, nothing launched);
+ *   - the first call on each device looks up that array's device address (and may load
+ *     the library's device code); make that first call before any stream capture;
+ *   - the call returns without synchronizing when dist2 is NULL (the work is queued on
+ *     stream); with dist2 it waits for the result;
+ *   - all calls share the one array: calls whose work overlaps on the GPU (different
+ *     streams or host threads without ordering) race and give undefined results. Each call
+ *     writes every scratch entry it reads, so nothing needs clearing between calls. */
+int mcf_project_capped_simplex_noalloc(int32_t n, int32_t m, int32_t ld, const float* Qt,
+                                       const float* cap, float* Ft, float* mu, double* dist2,
+                                       void* stream);
+
 /* Launch shape table: shape s gives `group` threads per edge/node, each holding `vpt`
  * 16-byte chunks of the edge/node vector (capacity group*vpt chunks of 16 bytes of F).
  * Returns the number of shapes; fills the three arrays (may be NULL) up to that count. */

@@ -66,7 +66,8 @@ SYMBOLS = [
     "mcf_create_problem", "mcf_update_capacities", "mcf_update_weights",
     "mcf_destroy_problem", "mcf_problem_size", "mcf_problem_device_bytes",
     "mcf_options_default", "mcf_solve", "mcf_solve_timed", "mcf_submit", "mcf_poll", "mcf_wait",
-    "mcf_cancel", "mcf_serving_config", "mcf_project_capped_simplex", "mcf_shape_info",
+    "mcf_cancel", "mcf_serving_config", "mcf_project_capped_simplex",
+    "mcf_project_capped_simplex_noalloc", "mcf_shape_info",
     "mcf_last_error", "mcf_version",
 ]
 
@@ -99,6 +100,8 @@ def _load() -> C.CDLL:
         "mcf_serving_config": (C.c_int, [C.c_int64, C.c_int]),
         "mcf_project_capped_simplex": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P, P, P,
                                                  dp, P]),
+        "mcf_project_capped_simplex_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P, P,
+                                                         P, dp, P]),
         "mcf_shape_info": (C.c_int, [ip, ip, ip]),
         "mcf_last_error": (C.c_char_p, []),
         "mcf_version": (C.c_char_p, []),
@@ -296,6 +299,18 @@ def mcf_project_capped_simplex(n: int, m: int, ld: int, Qt_ptr: int, cap_ptr: in
                                         C.byref(d2), stream or None)
     if rc != MCF_OK:
         raise MCFError(rc, "mcf_project_capped_simplex")
+    return d2.value
+
+
+def mcf_project_capped_simplex_noalloc(n: int, m: int, ld: int, Qt_ptr: int, cap_ptr: int,
+                                       Ft_ptr: int, mu_ptr: int, stream: int = 0) -> float:
+    """As mcf_project_capped_simplex, for callers that cannot allocate device memory (the
+    scratch is a fixed array in the library; m <= 262144). Returns sum ||F - Q||^2."""
+    d2 = C.c_double(0.0)
+    rc = LIB.mcf_project_capped_simplex_noalloc(int(n), int(m), int(ld), Qt_ptr, cap_ptr, Ft_ptr,
+                                                mu_ptr, C.byref(d2), stream or None)
+    if rc != MCF_OK:
+        raise MCFError(rc, "mcf_project_capped_simplex_noalloc")
     return d2.value
 
 
