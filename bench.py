@@ -53,6 +53,8 @@ WORKLOADS = {
                                                              gamma=0.5, name="prof"),
                  sample=lambda seed: I.large_slice(seed),
                  desc="n=10000, m=20000 (ring + 1 random out-edge per node), large recipe"),
+    "batched": dict(factory=None, sample=None, desc="64 uneven instances (see run_batched)"),
+    "served": dict(factory=None, sample=None, desc="Poisson request stream (see run_served)"),
     "mid": dict(factory=lambda seed: I.mid(seed), sample=lambda seed: I.mid(seed),
                 desc="n=100, m=1000 (ring + 9 random out-edges per node), c~U[1,10], "
                      "u = w log s, w~U[0.5,1.5]"),
@@ -230,7 +232,7 @@ def run_ours(args, rank, world, local_rank):
     s_f = {"fp32": 4, "bf16": 2, "fp64": 8}[prec]
     s_p = 8 if prec == "fp64" else 4
     common = dict(precision=prec, device=local_rank, k_check=args.k_check,
-                  cuda_stream=stream.cuda_stream, stop_mode="none")
+                  cuda_stream=stream.cuda_stream, stop_mode="none", shape=args.shape)
 
     def barrier():
         if world > 1:
@@ -249,11 +251,10 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
     barrier()
     ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * args.steps / (ms_max / 1e3)
+    from paper_2501_17996_gb300.sharding import aggregate_rate
+
+    value, t_max = aggregate_rate(args.steps, ms / 1e3, world, device="cuda")
+    ms_max = t_max * 1e3
     launches = sum(v[1] for k, v in times.items() if k != "ms_total")
 
     # ---- roofline of the dominant kernel
@@ -287,10 +288,9 @@ def run_ours(args, rank, world, local_rank):
         with B.Problem(inst) as p2:
             p2.solve(want_T=True, max_iters=args.steps, **common)
         t_e2e = time.perf_counter() - t0
-        tt = torch.tensor([t_e2e], device="cuda")
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_value = world * args.steps / float(tt.item())
+        from paper_2501_17996_gb300.sharding import aggregate_rate
+
+        e2e_value, _ = aggregate_rate(args.steps, t_e2e, world, device="cuda")
     ld = (n + 7) // 8 * 8
     h2d = (n * ld * s_p) + m * s_p + (3 * m + 2 * (n + 1)) * 4     # W, cap, incidence
     d2h = n * ld * s_p                                             # T
@@ -315,7 +315,7 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: {wl['desc']}", "n": n, "m": m,
                    "precision": prec, "storage_F": {"fp32": "f32", "bf16": "bf16", "fp64": "f64"}[prec],
-                   "k_check": args.k_check, "seed": args.seed,
+                   "k_check": args.k_check, "seed": args.seed, "shape": args.shape,
                    "l2": "inputs larger than L2 (F alone is %.1f GB)" % (2 * s_f * n * m / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
@@ -338,6 +338,172 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args, rank, world, local_rank):
+    """cfg4: 64 instances, n ~ U[50,400], out-degree ~ U[4,16], half log / half power,
+    solved to relative KKT 1e-4 by one batched engine, against one-at-a-time solves."""
+    import torch
+
+    from paper_2501_17996_gb300 import binding as B
+
+    torch.cuda.set_device(local_rank)
+    insts = I.batched(seed=args.seed + rank, count=64)
+    probs = [B.Problem(i) for i in insts]
+    kw = dict(stop_mode="kkt", eps=1e-4, max_iters=200000, k_check=args.k_check, device=local_rank)
+    # warm-up: allocate device state for every problem, build graphs
+    B.mcf_solve_batch(probs, B.mcf_options_default(**{**kw, "stop_mode": "none", "max_iters": 50}))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, res = B.mcf_solve_batch(probs, B.mcf_options_default(**kw))
+    t_batch = time.perf_counter() - t0
+    iters = [r["iters"] for r in res]
+    t0 = time.perf_counter()
+    lat = []
+    for p in probs:
+        t1 = time.perf_counter()
+        p.solve(want_T=False, **kw)
+        lat.append(time.perf_counter() - t1)
+    t_seq = time.perf_counter() - t0
+    for p in probs:
+        p.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": len(insts) / t_batch, "unit": "solves/s", "n_gpus": world,
+        "steps": 1, "warmup": 1, "ms_per_step": t_batch * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batched: 64 instances, n~U[50,400], out-degree~U[4,16], "
+                               "c~U[1,10], half log / half power gamma~U[0.3,0.7]",
+                   "stop": "rel_kkt < 1e-4", "k_check": args.k_check},
+        "batched": {"seconds": t_batch, "solves_per_s": len(insts) / t_batch, "rc": rc,
+                    "iters_total": int(sum(iters)), "iters_max": int(max(iters)),
+                    "all_converged": all(r["status"] == 0 for r in res)},
+        "one_at_a_time": {"seconds": t_seq, "solves_per_s": len(insts) / t_seq,
+                          "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99))},
+        "speedup": t_seq / t_batch,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_served(args, rank, world, local_rank):
+    """cfg5: Poisson stream of solves (mean --rate req/s for --window s) over resident
+    networks with n in {100, 300, 1000, 3000} (out-degree 8, log utility): 70% warm
+    re-solves after a +-10% perturbation of capacities or weights, 30% cold solves (a cold
+    start of a resident network stands for a new network of that size; the host-side
+    creation of new networks is left out of the trace). Served by continuous batching
+    (mcf_submit/mcf_poll), then the same trace one request at a time with mcf_solve.
+    Latency = completion time - arrival time; stop rule rel_kkt < 1e-4."""
+    import threading
+
+    from paper_2501_17996_gb300 import binding as B
+
+    rng = np.random.default_rng(args.seed + 1000 * rank)
+    sizes = [100, 300, 1000, 3000]
+    per = args.pool
+    nets = []
+    for n in sizes:
+        for k in range(per):
+            inst = I.served_network(n, seed=args.seed * 100003 + n * 97 + k)
+            nets.append((inst, B.Problem(inst)))
+    kw = dict(stop_mode="kkt", eps=1e-4, max_iters=100000, k_check=args.k_check, device=local_rank)
+    # warm-up: every network solved once (device state resident, graphs built)
+    for t in [p.submit(**kw) for _, p in nets]:
+        B.mcf_wait(t, -1)
+    # trace
+    arrivals = []
+    tcur = 0.0
+    while True:
+        tcur += rng.exponential(1.0 / args.rate)
+        if tcur > args.window:
+            break
+        warm = rng.random() < 0.7
+        what = "cap" if rng.random() < 0.5 else "w"
+        arrivals.append((tcur, int(rng.integers(len(nets))), warm, what, int(rng.integers(1 << 30))))
+    originals = [(inst.cap.copy(), inst.w.copy()) for inst, _ in nets]
+
+    def apply(idx, what, seed):
+        inst, p = nets[idx]
+        prng = np.random.default_rng(seed)
+        base = I.Instance(inst.n, inst.tail, inst.head, originals[idx][0], inst.kind, originals[idx][1])
+        pert = I.perturb(base, 0.1, what, prng)
+        if what == "cap":
+            p.update_capacities(pert.cap)
+        else:
+            p.update_weights(pert.w)
+
+    def run_trace(mode):
+        lat = [None] * len(arrivals)
+        busy = set()
+        pending = {}
+        lock = threading.Lock()
+        t0 = time.perf_counter()
+        deferred = []
+        idx = 0
+        done = 0
+        iters = []
+        while done < len(arrivals):
+            now = time.perf_counter() - t0
+            # submit everything that has arrived and whose network is idle
+            while idx < len(arrivals) and arrivals[idx][0] <= now:
+                deferred.append(idx)
+                idx += 1
+            still = []
+            for r in deferred:
+                ta, net, warm, what, seed = arrivals[r]
+                if net in busy:
+                    still.append(r)
+                    continue
+                apply(net, what, seed)
+                opts = dict(kw, warm_start=1 if warm else 0)
+                if mode == "served":
+                    pending[nets[net][1].submit(**opts)] = (r, net)
+                    busy.add(net)
+                else:
+                    res = nets[net][1].solve(want_T=False, raise_on_error=False, **opts)
+                    lat[r] = time.perf_counter() - t0 - ta
+                    iters.append(res["iters"])
+                    done += 1
+            deferred = still
+            if mode == "served":
+                for tk in list(pending):
+                    res = B.mcf_poll(tk)
+                    if res is None:
+                        continue
+                    r, net = pending.pop(tk)
+                    lat[r] = time.perf_counter() - t0 - arrivals[r][0]
+                    iters.append(res["iters"])
+                    busy.discard(net)
+                    done += 1
+                time.sleep(0.0005)
+            if time.perf_counter() - t0 > args.window + args.drain_limit:
+                break
+        wall = time.perf_counter() - t0
+        got = [x for x in lat if x is not None]
+        return {"completed": len(got), "offered": len(arrivals), "wall_s": wall,
+                "solves_per_s": len(got) / wall if wall > 0 else None,
+                "p50_s": float(np.percentile(got, 50)) if got else None,
+                "p99_s": float(np.percentile(got, 99)) if got else None,
+                "mean_iters": float(np.mean(iters)) if iters else None}
+
+    served = run_trace("served")
+    serial = run_trace("serial")
+    for _, p in nets:
+        p.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": served["p99_s"], "unit": "s (p99 latency)", "n_gpus": world,
+        "steps": served["completed"], "warmup": 1, "ms_per_step": None,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "served: Poisson %.0f req/s for %.0f s, n in {100,300,1000,3000}, "
+                               "out-degree 8, 70%% warm (+-10%% c or w), 30%% cold, "
+                               "rel_kkt < 1e-4, 120 GB budget" % (args.rate, args.window),
+                   "networks": len(nets)},
+        "served": served, "one_at_a_time": serial,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -348,11 +514,16 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
     ap.add_argument("--k-check", dest="k_check", type=int, default=50)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--shape", type=int, default=-1, help="kernel shape index (-1 = automatic)")
     ap.add_argument("--ttt", action="store_true", help="also time a solve to --ttt-eps")
     ap.add_argument("--ttt-eps", dest="ttt_eps", type=float, default=1e-4)
     ap.add_argument("--ttt-max-iters", dest="ttt_max_iters", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
     ap.add_argument("--no-e2e", dest="no_e2e", action="store_true")
+    ap.add_argument("--rate", type=float, default=200.0, help="served: mean arrivals per s")
+    ap.add_argument("--window", type=float, default=5.0, help="served: arrival window (s)")
+    ap.add_argument("--pool", type=int, default=6, help="served: networks per size")
+    ap.add_argument("--drain-limit", dest="drain_limit", type=float, default=60.0)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -368,7 +539,12 @@ def main():
 
         torch.cuda.set_device(local_rank)
         dist.init_process_group("nccl")
-    run_ours(args, rank, world, local_rank)
+    if args.workload == "batched":
+        run_batched(args, rank, world, local_rank)
+    elif args.workload == "served":
+        run_served(args, rank, world, local_rank)
+    else:
+        run_ours(args, rank, world, local_rank)
     if world > 1:
         import torch.distributed as dist
 

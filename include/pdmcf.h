@@ -84,6 +84,11 @@ typedef struct mcf_options {
   int     device;            /* CUDA device ordinal (default 0)                             */
   void*   cuda_stream;       /* cudaStream_t to run on; NULL = the library's own stream     */
   double  omega0;            /* initial primal weight for cold starts (default 1.0)         */
+  int     stall_checks;      /* stop when the relative KKT measure has not improved by 5 %
+                                over this many consecutive checks while within 100x of eps
+                                (FP32 iterates reach a rounding floor); 0 = never. The result
+                                then has stalled = 1 and status MCF_ERR_NOT_CONVERGED.
+                                Default 20                                                  */
   int     shape;             /* kernel launch shape index (-1 = automatic); see
                                 mcf_shape_info. Lets tests and the tuner pick any shape
                                 whose capacity covers the problem                          */
@@ -109,6 +114,7 @@ typedef struct mcf_result {
   double  rel_kkt;     /* max(rel_gap, rel_cons, rel_stat)                             */
   double  nonpos_frac; /* fraction of off-diagonal T_ij <= 0 (Sec. 3.1 diagnostic)      */
   double  omega;       /* final primal weight                                          */
+  int     stalled;     /* 1 if the stall rule (mcf_options.stall_checks) ended the solve */
   double  seconds;     /* wall time of the call                                        */
 } mcf_result;
 
@@ -158,6 +164,18 @@ void mcf_options_default(mcf_options* o);
  * any non-NULL output buffers). Returns MCF_OK, MCF_ERR_NOT_CONVERGED (results filled),
  * MCF_ERR_NUMERIC, MCF_ERR_OOM, MCF_ERR_CUDA or MCF_ERR_INVALID. */
 int mcf_solve(mcf_problem* p, const mcf_options* opts, mcf_result* res);
+
+/* Solve `count` independent problems together on one GPU (FP32 iterates only): each PDHG
+ * phase is one launch per launch-shape class for all resident problems, every problem keeps
+ * its own step sizes, iteration count and stop test on the device, and its reductions are
+ * summed per edge and per node in a fixed order, so a problem's iterates are identical
+ * whether it is solved alone or in any batch. opts applies to every problem (warm_start = 1
+ * continues each problem's resident iterate). results[i] is filled as by mcf_solve for
+ * problems[i], including any output buffers it points to. The problems must be distinct
+ * and not in use by other calls. Returns MCF_OK if every problem met its stop rule, else
+ * the first other status (results are still filled). */
+int mcf_solve_batch(mcf_problem** problems, int count, const mcf_options* opts,
+                    mcf_result* results);
 
 /* Asynchronous solve: enqueue and return a ticket at once. The serving scheduler admits
  * the request when its device footprint fits the HBM budget (mcf_serving_config) and
@@ -242,8 +260,10 @@ int mcf_project_capped_simplex_noalloc(int32_t n, int32_t m, int32_t ld, const f
 
 /* Launch shape table: shape s gives `group` threads per edge/node, each holding `vpt`
  * 16-byte chunks of the edge/node vector (capacity group*vpt chunks of 16 bytes of F).
- * Returns the number of shapes; fills the three arrays (may be NULL) up to that count. */
-int mcf_shape_info(int* group, int* vpt, int* block);
+ * pipelined[s] = 1 marks the bulk-copy pipelined edge phase (one CTA per SM over
+ * head-aligned edge ranges; FP32 iterates only). Returns the number of shapes; fills the
+ * four arrays (each may be NULL) up to that count. */
+int mcf_shape_info(int* group, int* vpt, int* block, int* pipelined);
 
 /* Message for the last error of the calling thread ("" if none). */
 const char* mcf_last_error(void);

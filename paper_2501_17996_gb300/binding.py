@@ -41,7 +41,7 @@ class mcf_options(C.Structure):
         ("tau", C.c_double), ("omega_freeze_iter", C.c_int64), ("k_check", C.c_int),
         ("precision", C.c_int), ("warm_start", C.c_int), ("polish_iters", C.c_int),
         ("use_graphs", C.c_int), ("device", C.c_int), ("cuda_stream", C.c_void_p),
-        ("omega0", C.c_double), ("shape", C.c_int),
+        ("omega0", C.c_double), ("stall_checks", C.c_int), ("shape", C.c_int),
     ]
 
 
@@ -52,7 +52,7 @@ class mcf_result(C.Structure):
         ("utility", C.c_double), ("dual_bound", C.c_double), ("r", C.c_double),
         ("r_over_nm", C.c_double), ("rel_gap", C.c_double), ("rel_cons", C.c_double),
         ("rel_stat", C.c_double), ("rel_kkt", C.c_double), ("nonpos_frac", C.c_double),
-        ("omega", C.c_double), ("seconds", C.c_double),
+        ("omega", C.c_double), ("stalled", C.c_int), ("seconds", C.c_double),
     ]
 
 
@@ -65,7 +65,7 @@ KERNEL_KINDS = ("edge", "node", "check", "scalar")
 SYMBOLS = [
     "mcf_create_problem", "mcf_update_capacities", "mcf_update_weights",
     "mcf_destroy_problem", "mcf_problem_size", "mcf_problem_device_bytes",
-    "mcf_options_default", "mcf_solve", "mcf_solve_timed", "mcf_submit", "mcf_poll", "mcf_wait",
+    "mcf_options_default", "mcf_solve", "mcf_solve_timed", "mcf_solve_batch", "mcf_submit", "mcf_poll", "mcf_wait",
     "mcf_cancel", "mcf_serving_config", "mcf_project_capped_simplex",
     "mcf_project_capped_simplex_noalloc", "mcf_shape_info",
     "mcf_last_error", "mcf_version",
@@ -93,6 +93,8 @@ def _load() -> C.CDLL:
         "mcf_solve": (C.c_int, [P, C.POINTER(mcf_options), C.POINTER(mcf_result)]),
         "mcf_solve_timed": (C.c_int, [P, C.POINTER(mcf_options), C.POINTER(mcf_result),
                                       C.POINTER(mcf_kernel_times)]),
+        "mcf_solve_batch": (C.c_int, [C.POINTER(P), C.c_int, C.POINTER(mcf_options),
+                                      C.POINTER(mcf_result)]),
         "mcf_submit": (C.c_int, [P, C.POINTER(mcf_options), C.POINTER(C.c_int64)]),
         "mcf_poll": (C.c_int, [C.c_int64, C.POINTER(C.c_int), C.POINTER(mcf_result)]),
         "mcf_wait": (C.c_int, [C.c_int64, C.c_int64, C.POINTER(C.c_int), C.POINTER(mcf_result)]),
@@ -102,7 +104,7 @@ def _load() -> C.CDLL:
                                                  dp, P]),
         "mcf_project_capped_simplex_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P, P,
                                                          P, dp, P]),
-        "mcf_shape_info": (C.c_int, [ip, ip, ip]),
+        "mcf_shape_info": (C.c_int, [ip, ip, ip, ip]),
         "mcf_last_error": (C.c_char_p, []),
         "mcf_version": (C.c_char_p, []),
     }
@@ -140,13 +142,15 @@ def mcf_version() -> str:
     return LIB.mcf_version().decode()
 
 
-def mcf_shape_info() -> list[tuple[int, int, int]]:
-    cnt = LIB.mcf_shape_info(None, None, None)
+def mcf_shape_info() -> list[tuple[int, int, int, int]]:
+    """[(group, vpt, block, pipelined)] per shape index."""
+    cnt = LIB.mcf_shape_info(None, None, None, None)
     g = (C.c_int32 * cnt)()
     v = (C.c_int32 * cnt)()
     b = (C.c_int32 * cnt)()
-    LIB.mcf_shape_info(g, v, b)
-    return [(g[i], v[i], b[i]) for i in range(cnt)]
+    t = (C.c_int32 * cnt)()
+    LIB.mcf_shape_info(g, v, b, t)
+    return [(g[i], v[i], b[i], t[i]) for i in range(cnt)]
 
 
 def mcf_options_default(**overrides) -> mcf_options:
@@ -248,6 +252,22 @@ def mcf_solve_timed(h, opts: mcf_options, n, m, want_T=False) -> tuple[dict, dic
     out = _result_dict(res, bufs)
     out["rc"] = rc
     return out, times
+
+
+def mcf_solve_batch(problems, opts: mcf_options, want_T=False, want_Y=False) -> tuple[int, list]:
+    """problems: list of Problem. Returns (rc, [result dict per problem])."""
+    k = len(problems)
+    hs = (C.c_void_p * k)(*[p.h for p in problems])
+    results = (mcf_result * k)()
+    bufs = []
+    for i, p in enumerate(problems):
+        r, b = _result_struct(p.n, p.m, want_T, False, want_Y)
+        results[i] = r
+        bufs.append(b)
+    rc = LIB.mcf_solve_batch(hs, k, C.byref(opts), results)
+    if rc not in (MCF_OK, MCF_ERR_NOT_CONVERGED):
+        raise MCFError(rc, "mcf_solve_batch")
+    return rc, [_result_dict(results[i], bufs[i]) for i in range(k)]
 
 
 def mcf_submit(h, opts: mcf_options) -> int:

@@ -122,6 +122,7 @@ int validate_options(const mcf_options* o) {
   if (o->precision != MCF_FP32 && o->precision != MCF_FP64 && o->precision != MCF_BF16_F)
     return fail(MCF_ERR_INVALID, "unknown precision");
   if (o->polish_iters < 0) return fail(MCF_ERR_INVALID, "polish_iters must be >= 0");
+  if (o->stall_checks < 0) return fail(MCF_ERR_INVALID, "stall_checks must be >= 0");
   if (o->shape < -1 || o->shape >= mcf_shape_count()) return fail(MCF_ERR_INVALID, "unknown shape");
   return MCF_OK;
 }
@@ -155,6 +156,7 @@ void mcf_options_default(mcf_options* o) {
   o->device = 0;
   o->cuda_stream = nullptr;
   o->omega0 = 1.0;       // Sec. 2.5
+  o->stall_checks = 20;
   o->shape = -1;
 }
 

@@ -108,6 +108,48 @@ __device__ __forceinline__ void st_plain(T* p, const T (&v)[N]) {
   }
 }
 
+
+// ------------------------------------------------------------------ TMA bulk copies + mbarrier
+// 1-D bulk copies global -> shared (cp.async.bulk) completing on an mbarrier; sizes and
+// addresses are multiples of 16 bytes. Every wait is bounded.
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Returns false if the phase did not complete within the bound.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // ------------------------------------------------------------------ group reductions
 // A "group" is GROUP consecutive threads that own one edge (or node): a warp when
 // GROUP == 32, the whole block when GROUP == blockDim.x > 32. All threads of a group get
@@ -279,6 +321,76 @@ __device__ __forceinline__ P util_traffic(int kind, P y, P w, P g) {
   return pow(w * g / (-y), P(1) / (P(1) - g));
 }
 
+// ------------------------------------------------------------------ scalar tail
+
+// Deterministic sum of base[b*stride + field] over b < nb by 256 threads: contiguous
+// per-thread segments, then a fixed binary tree.
+static __device__ __forceinline__ double det_sum(const double* base, int nb, int stride, int field, double* sh) {
+  const int per = (nb + 255) / 256;
+  const int b0 = threadIdx.x * per;
+  const int b1 = min(nb, b0 + per);
+  double s = 0.0;
+  for (int b = b0; b < b1; ++b) s += base[(size_t)b * stride + field];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// Scalar tail of one iteration (thread 0 of the reducing block): Delta_F, Delta_Y, on check
+// iterations r (Eq. e-res), the dual bound and the relative KKT parts, then the primal weight
+// rule (Eq. e-primal_weight) and alpha/beta for the next iteration.
+static __device__ __forceinline__ void scalar_update(DevScalars* s, double dF2, double dY2,
+                                                     const double* nodep, const double* chk,
+                                                     bool check) {
+  const double inf = INFINITY;
+  const double dF = sqrt(dF2), dY = sqrt(dY2);
+  s->dF = dF;
+  s->dY = dY;
+  if (!isfinite(dF) || !isfinite(dY)) s->numeric_error = 1;
+  const long long k = s->k;
+  if (check) {
+    const double nonpos = nodep[1], Psum = nodep[2], conj = nodep[3], cons2 = nodep[4];
+    const double t2 = nodep[5], ybad = nodep[6];
+    const double g2 = chk[0], gd = chk[1], d2 = chk[2], lin = chk[3];
+    const bool feasible = nonpos == 0.0;
+    // Eq. (e-res): r = ||G||^2 - <G,D>^2/||D||^2 if D != 0 and <G,D> >= 0, else ||G||^2
+    double r = inf;
+    if (feasible) {
+      r = (d2 == 0.0 || gd < 0.0) ? g2 : g2 - gd * gd / d2;
+      if (r < 0.0) r = 0.0;
+    }
+    const double P = feasible ? Psum : -inf;
+    const double D = ybad > 0.0 ? inf : conj + lin;
+    s->feasible = feasible ? 1 : 0;
+    s->r = r;
+    s->P = P;
+    s->D = D;
+    s->g_norm = sqrt(g2);
+    s->rel_gap = (feasible && isfinite(D)) ? (D - P) / (1.0 + fabs(P) + fabs(D)) : inf;
+    s->rel_cons = ybad > 0.0 ? inf : sqrt(cons2) / (1.0 + sqrt(t2));
+    s->rel_stat = feasible ? sqrt(r) / (1.0 + sqrt(g2)) : inf;
+    s->rel_kkt = fmax(s->rel_gap, fmax(s->rel_cons, s->rel_stat));
+    s->nonpos_frac = nonpos / ((double)s->n * (double)(s->n - 1));
+    s->check_k = k + 1;
+    if (!isfinite(Psum) && feasible) s->numeric_error = 1;
+  }
+  // Algorithm 2.1, step 3 (Eq. e-primal_weight)
+  s->alpha_last = s->alpha;
+  s->beta_last = s->beta;
+  if (k % s->k_adapt == 0 && dF > s->tau && dY > s->tau && (s->freeze < 0 || k < s->freeze)) {
+    s->omega = pow(dY / dF, s->theta) * pow(s->omega, 1.0 - s->theta);
+  }
+  s->alpha = s->eta / s->omega;
+  s->beta = s->eta * s->omega;
+  s->k = k + 1;
+}
+
 // ------------------------------------------------------------------ kernel arguments
 
 template <typename P, typename S>
@@ -304,6 +416,8 @@ struct IterArgs {
   double* part_edge;  // [grid_edge]
   double* part_node;  // [grid_node * NODE_PARTS]
   double* part_check; // [grid_edge * CHECK_PARTS]
+  P* Pin;             // n x ld: sum_{in(j)} F^{k+1/2} per head j (pipelined edge phase only)
+  const int32_t* cta_ptr;  // [grid + 1] head-aligned edge ranges of the pipelined edge phase
   DevScalars* sc;
   P rho;
   int parity;         // F[parity], Y[parity] hold F^{k-1/2}, Y^k; the other slot receives k+1
@@ -383,10 +497,19 @@ edge_kernel(IterArgs<P, S> a) {
   const P* __restrict__ Y = a.Y[a.parity];
   double dsum = 0.0;
 
+  int nh = 0, nt = 0;
+  P nc = P(0), nmu = P(0);
+  if (gid < a.m) { nh = a.e_head[gid]; nt = a.e_tail[gid]; nc = a.cap[gid]; nmu = a.mu[gid]; }
   for (int e = gid; e < a.m; e += ngroups) {
-    const int h = a.e_head[e], t = a.e_tail[e];
-    const P c = a.cap[e];
-    const P mu0 = a.mu[e];
+    const int h = nh, t = nt;
+    const P c = nc;
+    const P mu0 = nmu;
+    if (e + ngroups < a.m) {   // next edge's indices and scalars, one edge ahead
+      nh = a.e_head[e + ngroups];
+      nt = a.e_tail[e + ngroups];
+      nc = a.cap[e + ngroups];
+      nmu = a.mu[e + ngroups];
+    }
     const S* fo = Fo + (size_t)e * a.ld;
     const P* yh = Y + (size_t)h * a.ld;
     const P* yt = Y + (size_t)t * a.ld;
@@ -436,7 +559,7 @@ edge_kernel(IterArgs<P, S> a) {
 
 // ------------------------------------------------------------------ node phase
 
-template <typename P, typename S, int VPT, int GROUP, int BLOCK, int MINB>
+template <typename P, typename S, int VPT, int GROUP, int BLOCK, int MINB, bool PIN = false>
 __global__ void __launch_bounds__(BLOCK, MINB)
 node_kernel(IterArgs<P, S> a) {
   constexpr int VW = StoreTraits<S>::VW;
@@ -463,9 +586,18 @@ node_kernel(IterArgs<P, S> a) {
     for (int v = 0; v < VPT; ++v)
 #pragma unroll
       for (int u = 0; u < VW; ++u) s[v][u] = P(0);
-    // p_j = sum_{in(j)} f_new - sum_{out(j)} f_new, two edge rows in flight per step
-    const int ib = a.in_ptr[j], nin = a.in_ptr[j + 1] - ib;
+    // p_j = sum_{in(j)} f_new - sum_{out(j)} f_new, two edge rows in flight per step. With
+    // PIN the edge phase already summed the in-edges into Pin[j].
+    const int ib = a.in_ptr[j], nin = PIN ? 0 : a.in_ptr[j + 1] - ib;
     const int ob = a.out_ptr[j], deg = nin + (a.out_ptr[j + 1] - ob);
+    if constexpr (PIN) {
+      const P* pr = a.Pin + (size_t)j * a.ld;
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        const int ci = v * GROUP + lane;
+        if (ci < nchunks) ld_plain<P, VW>(pr + ci * VW, s[v]);
+      }
+    }
     auto row = [&](int k) -> const S* {
       return Fn + (size_t)(k < nin ? ib + k : a.out_idx[ob + k - nin]) * a.ld;
     };
@@ -568,6 +700,162 @@ node_kernel(IterArgs<P, S> a) {
     for (int k = 0; k < NODE_PARTS; ++k) acc[k] += (double)loc[k];
   }
   block_sum_write<BLOCK, NODE_PARTS>(acc, a.part_node + (size_t)blockIdx.x * NODE_PARTS);
+}
+
+
+// ------------------------------------------------------------------ pipelined edge phase
+// Large n: one CTA of 512 threads per SM walks a contiguous, head-aligned range of edges.
+// The F^{k-1/2} row and the Y_{:,tail} row of each edge arrive in shared memory by 1-D bulk
+// copies into two stages; as soon as edge i has been read into registers its stage is
+// refilled with edge i+2, so the copies overlap edge i's projection and edge i+1 is ready
+// when edge i is stored. Y_{:,head} stays in registers for the whole head group, and the
+// group's in-sum of F^{k+1/2} is written to Pin[head] so the node phase only gathers
+// out-edges.
+template <typename S, int VPT, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1)
+edge_tma_kernel(IterArgs<float, S> a) {
+  using P = float;
+  constexpr int VW = StoreTraits<S>::VW;
+  extern __shared__ __align__(128) unsigned char dyn[];
+  __shared__ __align__(8) uint64_t full[2];
+  __shared__ GroupScratch<BLOCK> sh;
+  __shared__ int ok_flag;
+  int phase = 0;
+  const int tid = threadIdx.x;
+  const int nchunks = a.ld / VW;
+  const uint32_t frow = (uint32_t)a.ld * (uint32_t)sizeof(S);
+  const uint32_t yrow = (uint32_t)a.ld * (uint32_t)sizeof(P);
+  S* sF[2] = {(S*)dyn, (S*)(dyn + frow + yrow)};
+  P* sY[2] = {(P*)(dyn + frow), (P*)(dyn + 2 * frow + yrow)};
+  const int e0 = a.cta_ptr[blockIdx.x];
+  const int cnt = a.cta_ptr[blockIdx.x + 1] - e0;
+  const P alpha = (P)a.sc->alpha;
+  const P rho = a.rho;
+  const S* __restrict__ Fo = a.F[a.parity];
+  S* __restrict__ Fn = a.F[a.parity ^ 1];
+  const P* __restrict__ Y = a.Y[a.parity];
+  if (tid == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    ok_flag = 1;
+    fence_proxy_async();
+  }
+  __syncthreads();
+  auto issue = [&](int i) {   // thread 0: bring edge e0+i into stage i&1
+    const int e = e0 + i, st = i & 1;
+    mbar_arrive_expect_tx(&full[st], frow + yrow);
+    tma_load_1d(sF[st], Fo + (size_t)e * a.ld, frow, &full[st]);
+    tma_load_1d(sY[st], Y + (size_t)a.e_tail[e] * a.ld, yrow, &full[st]);
+  };
+  if (tid == 0) {
+    if (cnt > 0) issue(0);
+    if (cnt > 1) issue(1);
+  }
+  double dsum = 0.0;
+  int cur_h = -1;
+  P yh[VPT][VW], sin_[VPT][VW];
+#pragma unroll
+  for (int v = 0; v < VPT; ++v)
+#pragma unroll
+    for (int u = 0; u < VW; ++u) { yh[v][u] = P(0); sin_[v][u] = P(0); }
+  // per-edge scalars of the next edge are fetched one edge ahead (off the critical path)
+  int nx_h = cnt > 0 ? a.e_head[e0] : 0;
+  P nx_c = cnt > 0 ? a.cap[e0] : P(0), nx_mu = cnt > 0 ? a.mu[e0] : P(0);
+
+  for (int i = 0; i < cnt; ++i) {
+    const int e = e0 + i, st = i & 1;
+    const int h = nx_h;
+    const P c_e = nx_c, mu_e = nx_mu;
+    if (i + 1 < cnt) {
+      nx_h = a.e_head[e + 1];
+      nx_c = a.cap[e + 1];
+      nx_mu = a.mu[e + 1];
+    }
+    if (h != cur_h) {   // new head group: flush the in-sum, fetch Y_{:,h} while we wait
+      if (cur_h >= 0) {
+        P* pr = a.Pin + (size_t)cur_h * a.ld;
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+          const int ci = v * BLOCK + tid;
+          if (ci < nchunks) st_plain<P, VW>(pr + ci * VW, sin_[v]);
+        }
+      }
+      const P* yr = Y + (size_t)h * a.ld;
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        const int ci = v * BLOCK + tid;
+        if (ci < nchunks) ld_keep<P, VW>(yr + ci * VW, yh[v]);
+#pragma unroll
+        for (int u = 0; u < VW; ++u) sin_[v][u] = P(0);
+      }
+      cur_h = h;
+    }
+    if (tid == 0 && !mbar_wait_bounded(&full[st], (uint32_t)((i >> 1) & 1))) ok_flag = 0;
+    __syncthreads();
+    if (!ok_flag) {   // a copy never completed: report, drain what is in flight, leave
+      if (tid == 0) {
+        a.sc->wait_timeout = 1;
+        mbar_wait_bounded(&full[st], (uint32_t)((i >> 1) & 1));
+        if (i + 1 < cnt) mbar_wait_bounded(&full[st ^ 1], (uint32_t)(((i + 1) >> 1) & 1));
+      }
+      return;
+    }
+    P f[VPT][VW], q[VPT][VW];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      const int ci = v * BLOCK + tid;
+      if (ci < nchunks) {
+        S fs[VW];
+        P yt[VW];
+        ld_plain<S, VW>(sF[st] + ci * VW, fs);
+        ld_plain<P, VW>(sY[st] + ci * VW, yt);
+#pragma unroll
+        for (int u = 0; u < VW; ++u) {
+          f[v][u] = to_p<P>(fs[u]);
+          q[v][u] = f[v][u] + alpha * (yh[v][u] - yt[u]);
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < VW; ++u) { f[v][u] = P(0); q[v][u] = P(0); }
+      }
+    }
+    __syncthreads();   // every thread is done with stage st: refill it with edge i+2
+    if (tid == 0 && i + 2 < cnt) {
+      fence_proxy_async();
+      issue(i + 2);
+    }
+    const P mu = project_mu<BLOCK, VPT, VW, P>(q, c_e, mu_e, sh, phase);
+    P dloc = P(0);
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      const int ci = v * BLOCK + tid;
+      if (ci < nchunks) {
+        S out[VW];
+#pragma unroll
+        for (int u = 0; u < VW; ++u) {
+          const P fh = q[v][u] > mu ? q[v][u] - mu : P(0);
+          out[u] = from_p<S, P>(rho * fh + (P(1) - rho) * f[v][u]);
+          const P fnew = to_p<P>(out[u]);
+          sin_[v][u] += fnew;
+          const P d = fnew - f[v][u];
+          dloc = fma(d, d, dloc);
+        }
+        st_stream<S, VW>(Fn + (size_t)e * a.ld + ci * VW, out);
+      }
+    }
+    dsum += (double)dloc;
+    if (tid == 0) a.mu[e] = mu;
+  }
+  if (cur_h >= 0) {
+    P* pr = a.Pin + (size_t)cur_h * a.ld;
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      const int ci = v * BLOCK + tid;
+      if (ci < nchunks) st_plain<P, VW>(pr + ci * VW, sin_[v]);
+    }
+  }
+  double v1[1] = {dsum};
+  block_sum_write<BLOCK, 1>(v1, a.part_edge + blockIdx.x);
 }
 
 // ------------------------------------------------------------------ check (residual) phase

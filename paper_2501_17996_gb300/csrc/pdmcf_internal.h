@@ -46,6 +46,7 @@ struct mcf_problem {
 };
 
 namespace pdmcf {
+int validate_options(const mcf_options* o);   // pdmcf_capi.cpp
 // Implemented in pdmcf_solver.cu.
 int device_solve(mcf_problem* p, const mcf_options* o, mcf_result* res,
                  mcf_kernel_times* kt = nullptr);

@@ -27,6 +27,21 @@ struct KernelTable {
   void (*check[NUM_SHAPES])(IterArgs<P, S>);
 };
 
+// Pipelined (bulk-copy) edge phase for long vectors: one 512-thread CTA per SM, `vpt`
+// 16-byte chunks of F per thread; the matching node phase reads the per-head in-sums.
+constexpr int TMA_BLOCK = 512;
+constexpr int TMA_NODE_BLOCK = 512;
+constexpr int NUM_TMA = 5;
+constexpr int kTmaVpt[NUM_TMA] = {2, 3, 4, 5, 7};
+
+template <typename S>
+struct TmaTable {
+  void (*edge[NUM_TMA])(IterArgs<float, S>);
+  void (*node[NUM_TMA])(IterArgs<float, S>);
+};
+const TmaTable<float>& tma_table_f32();
+const TmaTable<__nv_bfloat16>& tma_table_bf16();
+
 const KernelTable<float, float>& table_f32();
 const KernelTable<double, double>& table_f64();
 const KernelTable<float, __nv_bfloat16>& table_bf16();
@@ -68,6 +83,13 @@ void fill_shape(KernelTable<P, S>& t) {
   constexpr int MBN = min_blocks_node<P, d.vpt, StoreTraits<S>::VW, d.block>();
   t.node[IDX] = node_kernel<P, S, d.vpt, d.group, d.block, MBN>;
   t.check[IDX] = check_kernel<P, S, d.vpt, d.group, d.block, MB>;
+}
+
+template <typename S, int IDX>
+void fill_tma(TmaTable<S>& t) {
+  constexpr int V = kTmaVpt[IDX];
+  t.edge[IDX] = edge_tma_kernel<S, V, TMA_BLOCK>;
+  t.node[IDX] = node_kernel<float, S, V, TMA_NODE_BLOCK, TMA_NODE_BLOCK, 1, true>;
 }
 
 // Defined in the pdmcf_kernels_<precision>_<part>.cu translation units (compiled in

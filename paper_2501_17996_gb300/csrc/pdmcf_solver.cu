@@ -9,12 +9,14 @@
 
 #include <algorithm>
 #include <chrono>
+#include <type_traits>
 #include <cmath>
 #include <cstring>
 #include <limits>
 #include <string>
 #include <vector>
 
+#include "pdmcf_batch.cuh"
 #include "pdmcf_internal.h"
 #include "pdmcf_kernels.h"
 
@@ -42,25 +44,6 @@ struct ScalarArgs {
   int check;
 };
 
-// Deterministic sum of base[b*stride + field] over b < nb by 256 threads: contiguous
-// per-thread segments, then a fixed binary tree.
-__device__ double det_sum(const double* base, int nb, int stride, int field, double* sh) {
-  const int per = (nb + 255) / 256;
-  const int b0 = threadIdx.x * per;
-  const int b1 = min(nb, b0 + per);
-  double s = 0.0;
-  for (int b = b0; b < b1; ++b) s += base[(size_t)b * stride + field];
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int off = 128; off > 0; off >>= 1) {
-    if (threadIdx.x < off) sh[threadIdx.x] += sh[threadIdx.x + off];
-    __syncthreads();
-  }
-  const double r = sh[0];
-  __syncthreads();
-  return r;
-}
-
 __global__ void __launch_bounds__(256) scalar_kernel(ScalarArgs a) {
   __shared__ double sh[256];
   const double dF2 = det_sum(a.pe, a.nbe, 1, 0, sh);
@@ -72,48 +55,7 @@ __global__ void __launch_bounds__(256) scalar_kernel(ScalarArgs a) {
     for (int f = 0; f < CHECK_PARTS; ++f) chk[f] = det_sum(a.pc, a.nbc, CHECK_PARTS, f, sh);
   }
   if (threadIdx.x != 0) return;
-  DevScalars* s = a.sc;
-  const double inf = INFINITY;
-  const double dF = sqrt(dF2), dY = sqrt(dY2);
-  s->dF = dF;
-  s->dY = dY;
-  if (!isfinite(dF) || !isfinite(dY)) s->numeric_error = 1;
-  const long long k = s->k;
-  if (a.check) {
-    const double nonpos = nodep[1], Psum = nodep[2], conj = nodep[3], cons2 = nodep[4];
-    const double t2 = nodep[5], ybad = nodep[6];
-    const double g2 = chk[0], gd = chk[1], d2 = chk[2], lin = chk[3];
-    const bool feasible = nonpos == 0.0;
-    // Eq. (e-res): r = ||G||^2 - <G,D>^2/||D||^2 if D != 0 and <G,D> >= 0, else ||G||^2
-    double r = inf;
-    if (feasible) {
-      r = (d2 == 0.0 || gd < 0.0) ? g2 : g2 - gd * gd / d2;
-      if (r < 0.0) r = 0.0;
-    }
-    const double P = feasible ? Psum : -inf;
-    const double D = ybad > 0.0 ? inf : conj + lin;
-    s->feasible = feasible ? 1 : 0;
-    s->r = r;
-    s->P = P;
-    s->D = D;
-    s->g_norm = sqrt(g2);
-    s->rel_gap = (feasible && isfinite(D)) ? (D - P) / (1.0 + fabs(P) + fabs(D)) : inf;
-    s->rel_cons = ybad > 0.0 ? inf : sqrt(cons2) / (1.0 + sqrt(t2));
-    s->rel_stat = feasible ? sqrt(r) / (1.0 + sqrt(g2)) : inf;
-    s->rel_kkt = fmax(s->rel_gap, fmax(s->rel_cons, s->rel_stat));
-    s->nonpos_frac = nonpos / ((double)s->n * (double)(s->n - 1));
-    s->check_k = k + 1;
-    if (!isfinite(Psum) && feasible) s->numeric_error = 1;
-  }
-  // Algorithm 2.1, step 3 (Eq. e-primal_weight)
-  s->alpha_last = s->alpha;
-  s->beta_last = s->beta;
-  if (k % s->k_adapt == 0 && dF > s->tau && dY > s->tau && (s->freeze < 0 || k < s->freeze)) {
-    s->omega = pow(dY / dF, s->theta) * pow(s->omega, 1.0 - s->theta);
-  }
-  s->alpha = s->eta / s->omega;
-  s->beta = s->eta * s->omega;
-  s->k = k + 1;
+  scalar_update(a.sc, dF2, dY2, nodep, chk, a.check != 0);
 }
 
 // ------------------------------------------------------------------ init / output kernels
@@ -161,6 +103,12 @@ struct DeviceState {
   DevScalars* sc_host = nullptr;
   cudaStream_t own_stream = nullptr;
   int shape = -1, auto_shape = -1, block = 0, grid_edge = 0, grid_node = 0, grid_check = 0;
+  int requested_shape = -1;   // mcf_options.shape the grids were configured for
+  // pipelined edge phase (tma >= 0): one CTA per SM over head-aligned edge ranges
+  int tma = -1, grid_tma = 0, grid_node_pin = 0;
+  size_t tma_smem = 0;
+  void* Pin = nullptr;
+  int32_t* cta_ptr = nullptr;
   int cur = 0;
   bool valid = false;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -208,7 +156,8 @@ static void free_state(DeviceState* d) {
   destroy_graphs(d);
   void* bufs[] = {d->F[0], d->F[1], d->Y[0], d->Y[1], d->Pm, d->W, d->G, d->mu, d->cap,
                   d->That, d->Uprime, d->Yhat, d->e_tail, d->e_head, d->in_ptr,
-                  d->out_ptr, d->out_idx, d->part_edge, d->part_node, d->part_check, d->sc};
+                  d->out_ptr, d->out_idx, d->part_edge, d->part_node, d->part_check, d->sc,
+                  d->Pin, d->cta_ptr};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (d->sc_host) cudaFreeHost(d->sc_host);
@@ -258,14 +207,54 @@ static int upload_data(mcf_problem* p, DeviceState* d, cudaStream_t st) {
   return MCF_OK;
 }
 
-int mcf_shape_count() { return NUM_SHAPES; }
+int mcf_shape_count() { return NUM_SHAPES + NUM_TMA; }
+
+template <typename S> const TmaTable<S>& get_tma_table();
+template <> const TmaTable<float>& get_tma_table<float>() { return tma_table_f32(); }
+template <> const TmaTable<__nv_bfloat16>& get_tma_table<__nv_bfloat16>() { return tma_table_bf16(); }
+
+// Pipelined path for shape index NUM_SHAPES + t (t < NUM_TMA); needs two stages of
+// (F row + Y row) in shared memory.
+template <typename S>
+static int setup_tma(DeviceState* d, int want) {
+  constexpr int VW = StoreTraits<S>::VW;
+  const int nchunks = (int)(d->ld / VW);
+  int t = -1;
+  if (want >= NUM_SHAPES) t = want - NUM_SHAPES;
+  if (t < 0) { d->tma = -1; return MCF_OK; }
+  if (kTmaVpt[t] * TMA_BLOCK < nchunks) {
+    set_error("pipelined shape too small for this problem");
+    return MCF_ERR_INVALID;
+  }
+  int smem_optin = 0, sms = 0;
+  CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d->device));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d->device));
+  const size_t smem = 2 * (size_t)d->ld * (sizeof(S) + sizeof(float));
+  if (smem + 4096 > (size_t)smem_optin) {
+    if (want >= NUM_SHAPES) {
+      set_error("rows too long for the pipelined edge phase's shared-memory stages");
+      return MCF_ERR_INVALID;
+    }
+    d->tma = -1;
+    return MCF_OK;
+  }
+  const TmaTable<S>& T = get_tma_table<S>();
+  CK(cudaFuncSetAttribute((const void*)T.edge[t], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int on = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&on, (const void*)T.node[t], TMA_NODE_BLOCK, 0));
+  d->tma = t;
+  d->tma_smem = smem;
+  d->grid_tma = std::max(1, std::min(sms, d->m));
+  d->grid_node_pin = std::max(1, std::min(d->n, std::max(1, on) * sms));
+  return MCF_OK;
+}
 
 template <typename P, typename S>
 static int setup_grids(DeviceState* d, int want) {
   const KernelTable<P, S>& T = get_table<P, S>();
   constexpr int VW = StoreTraits<S>::VW;
   const int nchunks = (int)(d->ld / VW);
-  const int shape = want >= 0 ? want : pick_shape(nchunks);
+  const int shape = (want >= 0 && want < NUM_SHAPES) ? want : pick_shape(nchunks);
   if (shape < 0 || T.edge[shape] == nullptr ||
       kShapes[shape].group * kShapes[shape].vpt < nchunks) {
     set_error("no kernel shape covers this problem size at this precision");
@@ -293,17 +282,61 @@ static int setup_grids(DeviceState* d, int want) {
 }
 
 static int configure_shape(DeviceState* d, int want) {
-  if (d->precision == MCF_FP64) return setup_grids<double, double>(d, want);
-  if (d->precision == MCF_BF16_F) return setup_grids<float, __nv_bfloat16>(d, want);
-  return setup_grids<float, float>(d, want);
+  if (d->precision == MCF_FP64) {
+    if (want >= NUM_SHAPES) {
+      set_error("the pipelined shapes need FP32 iterates");
+      return MCF_ERR_INVALID;
+    }
+    d->tma = -1;
+    return setup_grids<double, double>(d, want);
+  }
+  int rc;
+  if (d->precision == MCF_BF16_F) {
+    rc = setup_grids<float, __nv_bfloat16>(d, want);
+    if (rc == MCF_OK) rc = setup_tma<__nv_bfloat16>(d, want);
+  } else {
+    rc = setup_grids<float, float>(d, want);
+    if (rc == MCF_OK) rc = setup_tma<float>(d, want);
+  }
+  return rc;
+}
+
+// Head-aligned split of the edge range into grid_tma contiguous pieces of about m/grid
+// edges (edges are sorted by head, so a head's in-edges never straddle two CTAs).
+static int upload_cta_ranges(mcf_problem* p, DeviceState* d, cudaStream_t st) {
+  if (d->tma < 0) return MCF_OK;
+  const int G = d->grid_tma, n = d->n, m = d->m;
+  std::vector<int32_t> ptr(G + 1, m);
+  ptr[0] = 0;
+  int k = 1;
+  const std::vector<int32_t>& inp = p->topo.in_ptr;
+  for (int j = 0; j < n && k < G; ++j) {
+    const int end = inp[j + 1];
+    if ((long long)end * G >= (long long)k * m) ptr[k++] = end;
+  }
+  if (d->cta_ptr) cudaFree(d->cta_ptr);
+  d->cta_ptr = nullptr;
+  if (cudaMalloc((void**)&d->cta_ptr, (G + 1) * sizeof(int32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("device allocation failed");
+    return MCF_ERR_OOM;
+  }
+  if (!d->Pin && cudaMalloc(&d->Pin, (size_t)n * d->ld * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("device allocation failed");
+    return MCF_ERR_OOM;
+  }
+  CK(cudaMemcpyAsync(d->cta_ptr, ptr.data(), (G + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return MCF_OK;
 }
 
 // (Re)allocate the per-block partial arrays for the current grids.
 static int alloc_partials(DeviceState* d) {
   for (double** b : {&d->part_edge, &d->part_node, &d->part_check})
     if (*b) { cudaFree(*b); *b = nullptr; }
-  bool ok = cudaMalloc((void**)&d->part_edge, (size_t)std::max(d->grid_edge, 1) * sizeof(double)) == cudaSuccess &&
-            cudaMalloc((void**)&d->part_node, (size_t)std::max(d->grid_node, 1) * NODE_PARTS * sizeof(double)) == cudaSuccess &&
+  bool ok = cudaMalloc((void**)&d->part_edge, (size_t)std::max({d->grid_edge, d->grid_tma, 1}) * sizeof(double)) == cudaSuccess &&
+            cudaMalloc((void**)&d->part_node, (size_t)std::max({d->grid_node, d->grid_node_pin, 1}) * NODE_PARTS * sizeof(double)) == cudaSuccess &&
             cudaMalloc((void**)&d->part_check, (size_t)std::max(d->grid_check, 1) * CHECK_PARTS * sizeof(double)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -336,6 +369,7 @@ static int alloc_state(mcf_problem* p, int precision, int device, int shape, cud
   d->pbytes = elem_bytes_p(precision);
   int rc = configure_shape(d, shape);
   if (rc != MCF_OK) { free_state(d); return rc; }
+  d->requested_shape = shape;
   const size_t n = d->n, m = d->m, ld = d->ld;
   auto A = [&](void** ptr, size_t bytes) -> bool {
     if (cudaMalloc(ptr, bytes) != cudaSuccess) { cudaGetLastError(); return false; }
@@ -376,6 +410,8 @@ static int alloc_state(mcf_problem* p, int precision, int device, int shape, cud
   // the kernels read every chunk of every row, so pads must start at zero everywhere
   for (void* b : {d->That, d->Uprime, d->Yhat}) CK(cudaMemsetAsync(b, 0, n * ld * d->pbytes, st));
   CK(cudaStreamSynchronize(st));
+  rc = upload_cta_ranges(p, d, st);
+  if (rc != MCF_OK) { free_state(d); return rc; }
   p->data_dirty = true;
   *out = d;
   return MCF_OK;
@@ -418,8 +454,32 @@ static IterArgs<P, S> make_args(DeviceState* d, const mcf_problem* p, double rho
   a.part_check = d->part_check;
   a.sc = d->sc;
   a.rho = (P)rho;
+  a.Pin = (P*)d->Pin;
+  a.cta_ptr = d->cta_ptr;
   return a;
 }
+
+// Edge and node phase launches of one iteration (register shapes or the pipelined pair).
+template <typename P, typename S>
+static cudaError_t launch_phase(DeviceState* d, void** kargs, int which, cudaStream_t st) {
+  if constexpr (!std::is_same<P, double>::value) {
+    if (d->tma >= 0) {
+      const TmaTable<S>& T = get_tma_table<S>();
+      if (which == 0)
+        return cudaLaunchKernel((const void*)T.edge[d->tma], dim3(d->grid_tma), dim3(TMA_BLOCK),
+                                kargs, d->tma_smem, st);
+      return cudaLaunchKernel((const void*)T.node[d->tma], dim3(d->grid_node_pin),
+                              dim3(TMA_NODE_BLOCK), kargs, 0, st);
+    }
+  }
+  const KernelTable<P, S>& T = get_table<P, S>();
+  if (which == 0)
+    return cudaLaunchKernel((const void*)T.edge[d->shape], dim3(d->grid_edge), dim3(d->block), kargs, 0, st);
+  return cudaLaunchKernel((const void*)T.node[d->shape], dim3(d->grid_node), dim3(d->block), kargs, 0, st);
+}
+
+static int edge_blocks(const DeviceState* d) { return d->tma >= 0 ? d->grid_tma : d->grid_edge; }
+static int node_blocks(const DeviceState* d) { return d->tma >= 0 ? d->grid_node_pin : d->grid_node; }
 
 template <typename P, typename S>
 static cudaError_t launch_iteration(DeviceState* d, IterArgs<P, S> a, int parity, bool check,
@@ -429,15 +489,15 @@ static cudaError_t launch_iteration(DeviceState* d, IterArgs<P, S> a, int parity
   a.check = check ? 1 : 0;
   void* kargs[] = {&a};
   cudaError_t e;
-  e = cudaLaunchKernel((const void*)T.edge[d->shape], dim3(d->grid_edge), dim3(d->block), kargs, 0, st);
+  e = launch_phase<P, S>(d, kargs, 0, st);
   if (e != cudaSuccess) return e;
-  e = cudaLaunchKernel((const void*)T.node[d->shape], dim3(d->grid_node), dim3(d->block), kargs, 0, st);
+  e = launch_phase<P, S>(d, kargs, 1, st);
   if (e != cudaSuccess) return e;
   if (check) {
     e = cudaLaunchKernel((const void*)T.check[d->shape], dim3(d->grid_check), dim3(d->block), kargs, 0, st);
     if (e != cudaSuccess) return e;
   }
-  ScalarArgs sa{d->sc, d->part_edge, d->grid_edge, d->part_node, d->grid_node,
+  ScalarArgs sa{d->sc, d->part_edge, edge_blocks(d), d->part_node, node_blocks(d),
                 d->part_check, d->grid_check, check ? 1 : 0};
   scalar_kernel<<<1, 256, 0, st>>>(sa);
   return cudaGetLastError();
@@ -472,10 +532,10 @@ static cudaError_t launch_iteration_timed(DeviceState* d, IterArgs<P, S> a, int 
   void* kargs[] = {&a};
   cudaError_t e;
   if (pool.used == 0) cudaEventRecord(pool.next(-1), st);
-  e = cudaLaunchKernel((const void*)T.edge[d->shape], dim3(d->grid_edge), dim3(d->block), kargs, 0, st);
+  e = launch_phase<P, S>(d, kargs, 0, st);
   if (e != cudaSuccess) return e;
   cudaEventRecord(pool.next(0), st);
-  e = cudaLaunchKernel((const void*)T.node[d->shape], dim3(d->grid_node), dim3(d->block), kargs, 0, st);
+  e = launch_phase<P, S>(d, kargs, 1, st);
   if (e != cudaSuccess) return e;
   cudaEventRecord(pool.next(1), st);
   if (check) {
@@ -483,7 +543,7 @@ static cudaError_t launch_iteration_timed(DeviceState* d, IterArgs<P, S> a, int 
     if (e != cudaSuccess) return e;
     cudaEventRecord(pool.next(2), st);
   }
-  ScalarArgs sa{d->sc, d->part_edge, d->grid_edge, d->part_node, d->grid_node,
+  ScalarArgs sa{d->sc, d->part_edge, edge_blocks(d), d->part_node, node_blocks(d),
                 d->part_check, d->grid_check, check ? 1 : 0};
   scalar_kernel<<<1, 256, 0, st>>>(sa);
   cudaEventRecord(pool.next(3), st);
@@ -547,9 +607,18 @@ static void fill_scalars(const DevScalars& s, const mcf_problem* p, mcf_result* 
   res->omega = s.omega;
 }
 
+// Extra stop rules of the BF16 phase that precedes an FP32 polish: hand off once the
+// relative KKT is within `handoff` of the target, or when it has not improved by 5 % over
+// `stall_checks` consecutive checks (BF16 rounding of F sets a floor on the accuracy).
+struct PhaseRule {
+  double handoff = 0.0;
+  int stall_checks = 0;
+  bool skip_outputs = false;
+};
+
 template <typename P, typename S>
 static int solve_t(mcf_problem* p, DeviceState* d, const mcf_options* o, mcf_result* res,
-                   cudaStream_t st, mcf_kernel_times* kt) {
+                   cudaStream_t st, mcf_kernel_times* kt, const PhaseRule& rule = PhaseRule()) {
   const int n = d->n;
   const size_t ld = d->ld, m = d->m;
   if (p->data_dirty) {
@@ -600,6 +669,11 @@ static int solve_t(mcf_problem* p, DeviceState* d, const mcf_options* o, mcf_res
   }
   int parity = d->cur;
   int64_t k = 0;
+  double best_kkt = INFINITY;
+  int since_best = 0;
+  double floor_best = INFINITY;
+  int floor_since = 0;
+  bool stalled = false;
   int status = MCF_ERR_NOT_CONVERGED;
   if (o->stop_mode == MCF_STOP_NONE) status = MCF_OK;
   bool any = false;
@@ -628,6 +702,11 @@ static int solve_t(mcf_problem* p, DeviceState* d, const mcf_options* o, mcf_res
     any = true;
     d->cur = parity;
     d->valid = true;
+    if (h.wait_timeout) {
+      set_error("a bounded device-side wait timed out; the iteration was abandoned");
+      d->valid = false;
+      return MCF_ERR_CUDA;
+    }
     if (h.numeric_error) {
       status = MCF_ERR_NUMERIC;
       set_error("NaN or Inf in the iterates");
@@ -635,6 +714,15 @@ static int solve_t(mcf_problem* p, DeviceState* d, const mcf_options* o, mcf_res
     }
     if (o->stop_mode == MCF_STOP_PAPER && h.r < (double)n * (double)m * o->eps) { status = MCF_OK; break; }
     if (o->stop_mode == MCF_STOP_REL_KKT && h.rel_kkt < o->eps) { status = MCF_OK; break; }
+    if (rule.handoff > 0.0 && h.rel_kkt < rule.handoff) break;
+    if (o->stop_mode == MCF_STOP_REL_KKT && o->stall_checks > 0 && h.rel_kkt < 100.0 * o->eps) {
+      if (h.rel_kkt < 0.95 * floor_best) { floor_best = h.rel_kkt; floor_since = 0; }
+      else if (++floor_since >= o->stall_checks) { stalled = true; break; }
+    }
+    if (rule.stall_checks > 0) {
+      if (h.rel_kkt < 0.95 * best_kkt) { best_kkt = h.rel_kkt; since_best = 0; }
+      else if (++since_best >= rule.stall_checks) break;
+    }
   }
   p->omega = h.omega;
   if (!any) {
@@ -643,7 +731,8 @@ static int solve_t(mcf_problem* p, DeviceState* d, const mcf_options* o, mcf_res
   }
   fill_scalars(h, p, res);
   res->status = status;
-  if (res->T || res->Y || res->F) {
+  res->stalled = stalled ? 1 : 0;
+  if (!rule.skip_outputs && (res->T || res->Y || res->F)) {
     int rc = device_copy_outputs(p, res);
     if (rc != MCF_OK) return rc;
   }
@@ -696,13 +785,16 @@ static int copy_outputs_t(mcf_problem* p, DeviceState* d, mcf_result* res, cudaS
 
 }  // namespace pdmcf
 
-extern "C" int mcf_shape_info(int* group, int* vpt, int* block) {
-  for (int s = 0; s < pdmcf::NUM_SHAPES; ++s) {
-    if (group) group[s] = pdmcf::kShapes[s].group;
-    if (vpt) vpt[s] = pdmcf::kShapes[s].vpt;
-    if (block) block[s] = pdmcf::kShapes[s].block;
+extern "C" int mcf_shape_info(int* group, int* vpt, int* block, int* pipelined) {
+  using namespace pdmcf;
+  for (int s = 0; s < NUM_SHAPES + NUM_TMA; ++s) {
+    const bool t = s >= NUM_SHAPES;
+    if (group) group[s] = t ? TMA_BLOCK : kShapes[s].group;
+    if (vpt) vpt[s] = t ? kTmaVpt[s - NUM_SHAPES] : kShapes[s].vpt;
+    if (block) block[s] = t ? TMA_BLOCK : kShapes[s].block;
+    if (pipelined) pipelined[s] = t ? 1 : 0;
   }
-  return pdmcf::NUM_SHAPES;
+  return NUM_SHAPES + NUM_TMA;
 }
 
 namespace pdmcf {
@@ -720,6 +812,110 @@ int device_copy_outputs(mcf_problem* p, mcf_result* res) {
   return copy_outputs_t<float, float>(p, d, res, st);
 }
 
+__global__ void bf16_to_f32_kernel(const __nv_bfloat16* src, float* dst, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x)
+    dst[i] = __bfloat162float(src[i]);
+}
+
+// Move the resident iterate of a BF16-storage state into a fresh FP32 state on the device:
+// F^{k-1/2} widened exactly, Y^k, P = F^{k-1/2} A^T and the projection multipliers copied.
+static int transfer_to_fp32(mcf_problem* p, const mcf_options* o, cudaStream_t st) {
+  DeviceState* src = p->ds;
+  DeviceState* dst = nullptr;
+  int rc = alloc_state(p, MCF_FP32, src->device, o->shape, (cudaStream_t)o->cuda_stream, &dst);
+  if (rc != MCF_OK) return rc;
+  dst->requested_shape = o->shape;
+  const size_t n = src->n, m = src->m, ld = src->ld;
+  const int c = src->cur;
+  bf16_to_f32_kernel<<<2048, 256, 0, st>>>((const __nv_bfloat16*)src->F[c], (float*)dst->F[c], m * ld);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dst->Y[c], src->Y[c], n * ld * 4, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dst->Pm, src->Pm, n * ld * 4, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dst->mu, src->mu, m * 4, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    free_state(dst);
+    set_error(std::string("CUDA error ") + cudaGetErrorString(e));
+    return MCF_ERR_CUDA;
+  }
+  dst->cur = c;
+  dst->valid = true;
+  free_state(src);
+  p->ds = dst;
+  p->data_dirty = true;
+  return MCF_OK;
+}
+
+// ------------------------------------------------------------------ batched-engine hooks
+
+// FP32 state on o->device for a batched run: cold start (F = 0, Y = I - 11^T, P = 0,
+// mu = 0, omega = omega0) unless a warm start is asked for and an iterate is resident.
+int batch_prepare_state(mcf_problem* p, const mcf_options* o, cudaStream_t st, bool* warm) {
+  if (p->ds && (p->ds->precision != MCF_FP32 || p->ds->device != o->device)) device_free(p);
+  if (!p->ds) {
+    int rc = alloc_state(p, MCF_FP32, o->device, -1, st, &p->ds);
+    if (rc != MCF_OK) return rc;
+  }
+  DeviceState* d = p->ds;
+  if (p->data_dirty) {
+    int rc = upload_data<float>(p, d, st);
+    if (rc != MCF_OK) return rc;
+  }
+  *warm = o->warm_start && d->valid;
+  const size_t n = d->n, m = d->m, ld = d->ld;
+  if (!*warm) {
+    d->cur = 0;
+    CK(cudaMemsetAsync(d->F[0], 0, m * ld * 4, st));
+    CK(cudaMemsetAsync(d->F[1], 0, m * ld * 4, st));
+    CK(cudaMemsetAsync(d->Pm, 0, n * ld * 4, st));
+    CK(cudaMemsetAsync(d->mu, 0, m * 4, st));
+    init_y_kernel<float><<<1024, 256, 0, st>>>((float*)d->Y[0], (int)n, (int)ld);
+    CK(cudaGetLastError());
+    p->omega = o->omega0 > 0 ? o->omega0 : 1.0;
+  }
+  CK(cudaStreamSynchronize(st));
+  d->valid = false;   // the iterate is in flux until the engine hands it back
+  return MCF_OK;
+}
+
+void batch_state_pointers(mcf_problem* p, BatchInst* bi, int* parity) {
+  DeviceState* d = p->ds;
+  *parity = d->cur;
+  bi->n = d->n;
+  bi->m = d->m;
+  bi->ld = d->ld;
+  bi->kind = p->kind;
+  bi->gamma = (float)p->gamma_scalar;
+  bi->e_tail = d->e_tail;
+  bi->e_head = d->e_head;
+  bi->in_ptr = d->in_ptr;
+  bi->out_ptr = d->out_ptr;
+  bi->out_idx = d->out_idx;
+  bi->cap = (const float*)d->cap;
+  bi->W = (const float*)d->W;
+  bi->Gm = (const float*)d->G;
+  bi->F[0] = (float*)d->F[0];
+  bi->F[1] = (float*)d->F[1];
+  bi->Y[0] = (float*)d->Y[0];
+  bi->Y[1] = (float*)d->Y[1];
+  bi->Pm = (float*)d->Pm;
+  bi->mu = (float*)d->mu;
+  bi->That = (float*)d->That;
+  bi->Uprime = (float*)d->Uprime;
+  bi->Yhat = (float*)d->Yhat;
+}
+
+// The engine's final scalars become the problem's resident state (warm starts, outputs).
+void batch_finish_state(mcf_problem* p, int parity, const DevScalars& s, cudaStream_t st) {
+  DeviceState* d = p->ds;
+  d->cur = parity;
+  d->valid = true;
+  p->omega = s.omega;
+  cudaMemcpyAsync(d->sc, &s, sizeof(DevScalars), cudaMemcpyHostToDevice, st);
+  cudaStreamSynchronize(st);
+}
+
 int device_solve(mcf_problem* p, const mcf_options* o, mcf_result* res, mcf_kernel_times* kt) {
   const int prec = o->precision;
   if (prec != MCF_FP32 && prec != MCF_FP64 && prec != MCF_BF16_F) {
@@ -734,16 +930,46 @@ int device_solve(mcf_problem* p, const mcf_options* o, mcf_result* res, mcf_kern
   }
   DeviceState* d = p->ds;
   CK(cudaSetDevice(d->device));
-  if (o->shape != d->shape && !(o->shape < 0 && d->shape == d->auto_shape)) {
+  if (o->shape != d->requested_shape) {
     // a different launch shape: new grids and partial arrays, same resident iterate
     int rc = configure_shape(d, o->shape);
     if (rc == MCF_OK) rc = alloc_partials(d);
+    if (rc == MCF_OK) rc = upload_cta_ranges(p, d, user ? user : d->own_stream);
     if (rc != MCF_OK) return rc;
+    d->requested_shape = o->shape;
     destroy_graphs(d);
   }
   cudaStream_t st = user ? user : d->own_stream;
   if (prec == MCF_FP64) return solve_t<double, double>(p, d, o, res, st, kt);
-  if (prec == MCF_BF16_F) return solve_t<float, __nv_bfloat16>(p, d, o, res, st, kt);
+  if (prec == MCF_BF16_F) {
+    if (o->polish_iters <= 0) return solve_t<float, __nv_bfloat16>(p, d, o, res, st, kt);
+    // BF16-stored F until close to the target (or stalled), then FP32 polish iterations.
+    PhaseRule rule;
+    rule.handoff = o->stop_mode == MCF_STOP_NONE ? 0.0 : 10.0 * o->eps;
+    rule.stall_checks = o->stop_mode == MCF_STOP_NONE ? 0 : 5;
+    rule.skip_outputs = true;
+    int rc = solve_t<float, __nv_bfloat16>(p, d, o, res, st, kt, rule);
+    if (rc != MCF_OK && rc != MCF_ERR_NOT_CONVERGED) return rc;
+    if (rc == MCF_OK && o->stop_mode != MCF_STOP_NONE) {
+      if (res->T || res->Y || res->F) return device_copy_outputs(p, res);
+      return rc;
+    }
+    const int64_t iters_bf16 = res->iters;
+    rc = transfer_to_fp32(p, o, st);
+    if (rc != MCF_OK) return rc;
+    mcf_options o2 = *o;
+    o2.precision = MCF_FP32;
+    o2.warm_start = 1;
+    o2.max_iters = o->polish_iters;
+    mcf_kernel_times kt2{};
+    cudaStream_t st2 = user ? user : p->ds->own_stream;   // the BF16 state's stream is gone
+    rc = solve_t<float, float>(p, p->ds, &o2, res, st2, kt ? &kt2 : nullptr);
+    if (kt)
+      for (int i = 0; i < 4; ++i) { kt->ms[i] += kt2.ms[i]; kt->launches[i] += kt2.launches[i]; }
+    if (kt) kt->ms_total += kt2.ms_total;
+    res->iters += iters_bf16;
+    return rc;
+  }
   return solve_t<float, float>(p, d, o, res, st, kt);
 }
 

@@ -25,6 +25,7 @@ struct DevScalars {
   double r, P, D, g_norm, rel_gap, rel_cons, rel_stat, rel_kkt, nonpos_frac;
   int feasible;
   int numeric_error;     // NaN/Inf met in a reduction
+  int wait_timeout;      // a bounded device-side wait gave up (kernel returned early)
   int n, m;
 };
 

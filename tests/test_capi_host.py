@@ -113,5 +113,6 @@ def test_solve_without_gpu_fails_loudly(lib):
 def test_shape_table(lib):
     shapes = lib.mcf_shape_info()
     assert len(shapes) >= 10
-    for g, v, b in shapes:
-        assert g in (32, 64, 128, 256, 512, 1024) and b % g == 0 and v >= 1
+    for g, v, b, t in shapes:
+        assert g in (32, 64, 128, 256, 512, 1024) and b % g == 0 and v >= 1 and t in (0, 1)
+    assert sum(t for *_, t in shapes) >= 1

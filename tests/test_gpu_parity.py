@@ -43,8 +43,8 @@ def shapes_for(lib, inst, precision):
     vw = {"fp32": 4, "fp64": 2, "bf16": 8}[precision]
     nchunks = ((inst.n + 7) // 8 * 8) // vw
     out = []
-    for s, (g, v, b) in enumerate(lib.mcf_shape_info()):
-        if g * v >= nchunks and not (precision == "fp64" and s >= 10):
+    for s, (g, v, b, piped) in enumerate(lib.mcf_shape_info()):
+        if g * v >= nchunks and not (precision == "fp64" and (s >= 10 or piped)):
             out.append(s)
     return out
 
@@ -115,6 +115,39 @@ def test_slice_trajectory_fp32(lib):
     assert rel_err(g["Y"], ref.Yhat, m) < 1e-4
 
 
+def test_slice_pipelined_shapes_fp32(lib):
+    """Every pipelined (bulk-copy) edge-phase shape on the n = 1000 slice: head groups of
+    several edges, head-aligned CTA ranges, in-sums consumed by the node phase."""
+    inst = I.large_slice(1)
+    K = 6
+    ref = oracle_k(inst, K)
+    m = off(inst.n)
+    piped = [s for s, (g, v, b, t) in enumerate(lib.mcf_shape_info()) if t]
+    assert piped
+    with lib.Problem(inst) as p:
+        for s in piped:
+            g = p.solve(precision="fp32", stop_mode="none", max_iters=K, k_check=3, shape=s,
+                        want_T=True, want_Y=True)
+            assert rel_err(g["T"], ref.T, m) < 1e-4, s
+            assert rel_err(g["Y"], ref.Yhat, m) < 1e-4, s
+
+
+def test_bf16_storage_every_shape_short_trajectory(lib):
+    """F stored as BF16 (8-bit mantissa) for every shape, 3 iterations: each stored F value
+    is rounded, so the bound is 1e-2 of scale; indexing mistakes give O(1) errors."""
+    inst = I.mid(0)
+    K = 3
+    ref = oracle_k(inst, K)
+    m = off(inst.n)
+    shapes = shapes_for(lib, inst, "bf16")
+    with lib.Problem(inst) as p:
+        for s in shapes:
+            g = p.solve(precision="bf16", stop_mode="none", max_iters=K, k_check=K, shape=s,
+                        want_T=True, want_Y=True)
+            assert rel_err(g["T"], ref.T, m) < 1e-2, s
+            assert rel_err(g["Y"], ref.Yhat, m) < 1e-2, s
+
+
 # ------------------------------------------------------------------ converged parity
 
 @pytest.mark.parametrize("name,precision,tol", [("tiny_s0", "fp64", 1e-6),
@@ -135,6 +168,22 @@ def test_converged_matches_oracle(lib, name, precision, tol):
     assert np.allclose(g["T"].sum(axis=1), 0, atol=1e-4 * np.abs(Tstar).max())
     assert g["feasible"] == 1 and g["rel_gap"] >= -1e-6
     assert g["utility"] <= g["dual_bound"] + 1e-6 * abs(g["dual_bound"])
+
+
+@pytest.mark.parametrize("name", ["mid_s0", "midpow_s0"])
+def test_bf16_with_fp32_polish_matches_oracle(lib, name):
+    """BF16-stored F until close to the target, then FP32 polish: the same acceptance
+    criterion as the FP32 path."""
+    gold = np.load(os.path.join(GOLDEN, f"oracle_{name}.npz"))
+    inst = {"mid_s0": lambda: I.mid(0), "midpow_s0": lambda: I.large(0, n=100)}[name]()
+    with lib.Problem(inst) as p:
+        g = p.solve(precision="bf16", polish_iters=100000, stop_mode="kkt", eps=1e-4,
+                    max_iters=200000, k_check=50, want_T=True)
+    assert g["rc"] == lib.MCF_OK and g["rel_kkt"] < 1e-4
+    m = off(inst.n)
+    Tstar = gold["T"]
+    assert abs(g["utility"] - float(gold["utility"])) <= 1e-4 * abs(float(gold["utility"]))
+    assert np.max(np.abs(g["T"][m] - Tstar[m]) / Tstar[m]) <= 1e-3
 
 
 # ------------------------------------------------------------------ closed forms and edges
@@ -195,19 +244,22 @@ def test_deterministic_and_graphs_equal_plain_launches(lib):
     assert r1["rel_kkt"] == r2["rel_kkt"] == r3["rel_kkt"]
 
 
-def test_async_matches_sync(lib):
+def test_async_matches_batched_and_sync(lib):
+    """Submitted requests run in the continuous-batching engine: identical to the same
+    problems solved by mcf_solve_batch, and within FP32 tolerance of mcf_solve."""
     insts = [I.mid(s) for s in range(3)] + [I.tiny(1)]
-    sync = []
-    for inst in insts:
-        with lib.Problem(inst) as p:
-            sync.append(p.solve(stop_mode="kkt", eps=1e-4, want_T=True))
     probs = [lib.Problem(inst) for inst in insts]
-    tickets = [p.submit(stop_mode="kkt", eps=1e-4) for p in probs]
-    for t, p, s in zip(tickets, probs, sync):
+    opts = dict(stop_mode="kkt", eps=1e-4)
+    sync = [p.solve(want_T=True, **opts) for p in probs]
+    _, batched = lib.mcf_solve_batch(probs, lib.mcf_options_default(**opts), want_T=True)
+    tickets = [p.submit(**opts) for p in probs]
+    for t, p, s, b in zip(tickets, probs, sync, batched):
         r = lib.mcf_wait(t, 120000, p.n, p.m, want_T=True)
         assert r is not None and r["status"] == lib.MCF_OK
-        assert r["iters"] == s["iters"]
-        assert np.array_equal(r["T"], s["T"])
+        assert r["iters"] == b["iters"]
+        assert np.array_equal(r["T"], b["T"])
+        m = off(p.n)
+        assert np.abs(r["T"][m] - s["T"][m]).max() <= 1e-3 * np.abs(s["T"][m]).max()
     for p in probs:
         p.close()
 
