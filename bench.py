@@ -449,7 +449,7 @@ def run_served(args, rank, world, local_rank):
             still = []
             for r in deferred:
                 ta, net, warm, what, seed = arrivals[r]
-                if net in busy:
+                if net in busy or time.perf_counter() - t0 > args.window + args.drain_limit:
                     still.append(r)
                     continue
                 apply(net, what, seed)

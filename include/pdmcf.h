@@ -89,6 +89,12 @@ typedef struct mcf_options {
                                 (FP32 iterates reach a rounding floor); 0 = never. The result
                                 then has stalled = 1 and status MCF_ERR_NOT_CONVERGED.
                                 Default 20                                                  */
+  int     compensated_duals; /* FP32/BF16 iterates: keep Y as an FP32 head plus a BF16 tail
+                                so the dual update is not limited by FP32 spacing of large
+                                duals (default 1; ignored for MCF_FP64)                     */
+  int     autotune;          /* batched and served solves: pick each size class's launch
+                                shape by timing candidates once per process on synthetic
+                                instances of that size (default 1)                         */
   int     shape;             /* kernel launch shape index (-1 = automatic); see
                                 mcf_shape_info. Lets tests and the tuner pick any shape
                                 whose capacity covers the problem                          */
@@ -115,6 +121,8 @@ typedef struct mcf_result {
   double  nonpos_frac; /* fraction of off-diagonal T_ij <= 0 (Sec. 3.1 diagnostic)      */
   double  omega;       /* final primal weight                                          */
   int     stalled;     /* 1 if the stall rule (mcf_options.stall_checks) ended the solve */
+  double  delta_f;     /* Delta_F of the last iteration (Eq. e-primal_weight)           */
+  double  delta_y;     /* Delta_Y of the last iteration                                 */
   double  seconds;     /* wall time of the call                                        */
 } mcf_result;
 
@@ -258,12 +266,22 @@ int mcf_project_capped_simplex_noalloc(int32_t n, int32_t m, int32_t ld, const f
                                        const float* cap, float* Ft, float* mu, double* dist2,
                                        void* stream);
 
+/* Time every launch shape that covers this problem (register shapes up to 4x the smallest
+ * sufficient capacity, and kinds 1 and 2 when opts->precision is not MCF_FP64) with
+ * 3 + 10 iterations each, and return the fastest in *best_shape (for mcf_options.shape) and
+ * its time per iteration in *ms_per_iter (may be NULL). Uses the problem's device state; the
+ * next solve of the problem starts cold. */
+int mcf_autotune(mcf_problem* p, const mcf_options* opts, int* best_shape, double* ms_per_iter);
+
 /* Launch shape table: shape s gives `group` threads per edge/node, each holding `vpt`
  * 16-byte chunks of the edge/node vector (capacity group*vpt chunks of 16 bytes of F).
- * pipelined[s] = 1 marks the bulk-copy pipelined edge phase (one CTA per SM over
- * head-aligned edge ranges; FP32 iterates only). Returns the number of shapes; fills the
- * four arrays (each may be NULL) up to that count. */
-int mcf_shape_info(int* group, int* vpt, int* block, int* pipelined);
+ * kind[s]: 0 register shapes (grid-stride over edges); 1 bulk-copy pipelined edge phase
+ * (cp.async.bulk into two shared-memory stages, one CTA per SM over head-aligned edge
+ * ranges); 2 register edge phase over head-aligned edge ranges with per-head in-sums in
+ * shared memory. Kinds 1 and 2 hand the in-sums to the node phase, need FP32 iterates, and
+ * kind 2 is the automatic choice for rows of 8 KB or more. Returns the number of shapes;
+ * fills the four arrays (each may be NULL) up to that count. */
+int mcf_shape_info(int* group, int* vpt, int* block, int* kind);
 
 /* Message for the last error of the calling thread ("" if none). */
 const char* mcf_last_error(void);

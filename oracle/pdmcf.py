@@ -154,9 +154,10 @@ def prox_pow(y, beta, w, gamma, max_newton: int = 200):
     On [t_lo, inf) h is increasing and convex, so Newton started at t_hi decreases
     monotonically to the root; it stops when a step no longer decreases t.
     """
-    y = np.asarray(y, dtype=np.float64)
-    w = np.broadcast_to(np.asarray(w, dtype=np.float64), y.shape)
-    g = np.broadcast_to(np.asarray(gamma, dtype=np.float64), y.shape)
+    shape = np.shape(y)
+    y = np.asarray(y, dtype=np.float64).ravel()
+    w = np.broadcast_to(np.asarray(w, dtype=np.float64), shape).ravel()
+    g = np.broadcast_to(np.asarray(gamma, dtype=np.float64), shape).ravel()
     c1 = g / (1.0 - g)
     c2 = beta * (1.0 / g - 1.0) * (w * g) ** (1.0 / (1.0 - g))
     k = c1 * c2
@@ -177,7 +178,7 @@ def prox_pow(y, beta, w, gamma, max_newton: int = 200):
         t[active] = t_new
         idx = np.flatnonzero(active)
         active[idx[~moved]] = False
-    return -t
+    return (-t).reshape(shape)
 
 
 # --------------------------------------------------------------------------- projection

@@ -41,7 +41,8 @@ class mcf_options(C.Structure):
         ("tau", C.c_double), ("omega_freeze_iter", C.c_int64), ("k_check", C.c_int),
         ("precision", C.c_int), ("warm_start", C.c_int), ("polish_iters", C.c_int),
         ("use_graphs", C.c_int), ("device", C.c_int), ("cuda_stream", C.c_void_p),
-        ("omega0", C.c_double), ("stall_checks", C.c_int), ("shape", C.c_int),
+        ("omega0", C.c_double), ("stall_checks", C.c_int), ("compensated_duals", C.c_int),
+        ("autotune", C.c_int), ("shape", C.c_int),
     ]
 
 
@@ -52,7 +53,8 @@ class mcf_result(C.Structure):
         ("utility", C.c_double), ("dual_bound", C.c_double), ("r", C.c_double),
         ("r_over_nm", C.c_double), ("rel_gap", C.c_double), ("rel_cons", C.c_double),
         ("rel_stat", C.c_double), ("rel_kkt", C.c_double), ("nonpos_frac", C.c_double),
-        ("omega", C.c_double), ("stalled", C.c_int), ("seconds", C.c_double),
+        ("omega", C.c_double), ("stalled", C.c_int), ("delta_f", C.c_double),
+        ("delta_y", C.c_double), ("seconds", C.c_double),
     ]
 
 
@@ -65,7 +67,8 @@ KERNEL_KINDS = ("edge", "node", "check", "scalar")
 SYMBOLS = [
     "mcf_create_problem", "mcf_update_capacities", "mcf_update_weights",
     "mcf_destroy_problem", "mcf_problem_size", "mcf_problem_device_bytes",
-    "mcf_options_default", "mcf_solve", "mcf_solve_timed", "mcf_solve_batch", "mcf_submit", "mcf_poll", "mcf_wait",
+    "mcf_options_default", "mcf_solve", "mcf_solve_timed", "mcf_solve_batch", "mcf_autotune",
+    "mcf_submit", "mcf_poll", "mcf_wait",
     "mcf_cancel", "mcf_serving_config", "mcf_project_capped_simplex",
     "mcf_project_capped_simplex_noalloc", "mcf_shape_info",
     "mcf_last_error", "mcf_version",
@@ -95,6 +98,8 @@ def _load() -> C.CDLL:
                                       C.POINTER(mcf_kernel_times)]),
         "mcf_solve_batch": (C.c_int, [C.POINTER(P), C.c_int, C.POINTER(mcf_options),
                                       C.POINTER(mcf_result)]),
+        "mcf_autotune": (C.c_int, [P, C.POINTER(mcf_options), C.POINTER(C.c_int),
+                                   C.POINTER(C.c_double)]),
         "mcf_submit": (C.c_int, [P, C.POINTER(mcf_options), C.POINTER(C.c_int64)]),
         "mcf_poll": (C.c_int, [C.c_int64, C.POINTER(C.c_int), C.POINTER(mcf_result)]),
         "mcf_wait": (C.c_int, [C.c_int64, C.c_int64, C.POINTER(C.c_int), C.POINTER(mcf_result)]),
@@ -143,7 +148,8 @@ def mcf_version() -> str:
 
 
 def mcf_shape_info() -> list[tuple[int, int, int, int]]:
-    """[(group, vpt, block, pipelined)] per shape index."""
+    """[(group, vpt, block, kind)] per shape index (kind 0 register, 1 bulk-copy pipelined,
+    2 register with in-sums)."""
     cnt = LIB.mcf_shape_info(None, None, None, None)
     g = (C.c_int32 * cnt)()
     v = (C.c_int32 * cnt)()
@@ -270,6 +276,16 @@ def mcf_solve_batch(problems, opts: mcf_options, want_T=False, want_Y=False) -> 
     return rc, [_result_dict(results[i], bufs[i]) for i in range(k)]
 
 
+def mcf_autotune(h, opts: mcf_options) -> tuple[int, float]:
+    """Returns (fastest shape index, ms per iteration)."""
+    shape = C.c_int(-1)
+    ms = C.c_double(0.0)
+    rc = LIB.mcf_autotune(h, C.byref(opts), C.byref(shape), C.byref(ms))
+    if rc != MCF_OK:
+        raise MCFError(rc, "mcf_autotune")
+    return shape.value, ms.value
+
+
 def mcf_submit(h, opts: mcf_options) -> int:
     t = C.c_int64()
     rc = LIB.mcf_submit(h, C.byref(opts), C.byref(t))
@@ -358,6 +374,9 @@ class Problem:
 
     def solve_timed(self, want_T=False, **opts):
         return mcf_solve_timed(self.h, mcf_options_default(**opts), self.n, self.m, want_T)
+
+    def autotune(self, **opts) -> tuple[int, float]:
+        return mcf_autotune(self.h, mcf_options_default(**opts))
 
     def submit(self, **opts) -> int:
         return mcf_submit(self.h, mcf_options_default(**opts))

@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -158,7 +159,8 @@ int BatchEngine::active_count() const {
   return a;
 }
 
-int BatchEngine::add(mcf_problem* p, const mcf_options& o, void* tag, int* slot_out) {
+int BatchEngine::add(mcf_problem* p, const mcf_options& o, void* tag, int* slot_out,
+                     int cls_override) {
   int s = -1;
   for (int i = 0; i < max_slots_ && s < 0; ++i)
     if (!slots_[i].used) s = i;
@@ -166,9 +168,10 @@ int BatchEngine::add(mcf_problem* p, const mcf_options& o, void* tag, int* slot_
     set_error("no free batch slot");
     return MCF_ERR_BUSY;
   }
-  const int cls = batch_admit_shape(p);
-  if (cls < 0) {
-    set_error("instance too large for the batched kernels");
+  const int nchunks = ((p->n + 7) / 8 * 8) / 4;
+  int cls = cls_override >= 0 ? cls_override : batch_admit_shape(p);
+  if (cls < 0 || kShapes[cls].group * kShapes[cls].vpt < nchunks) {
+    set_error("instance too large for the batched kernels or shape too small");
     return MCF_ERR_INVALID;
   }
   BCK(cudaSetDevice(device_));
@@ -369,6 +372,8 @@ void BatchEngine::release(int s) {
   r.rel_kkt = d.rel_kkt;
   r.nonpos_frac = d.nonpos_frac;
   r.omega = d.omega;
+  r.delta_f = d.dF;
+  r.delta_y = d.dY;
   r.stalled = h_sc_[s].stalled;
   r.status = sl.status;
   batch_finish_state(sl.p, h_sc_[s].parity, d, stream_);
@@ -381,6 +386,100 @@ void BatchEngine::release(int s) {
   sl.status = st;
   h_sc_[s].active = 0;
   lists_dirty_ = true;
+}
+
+// ------------------------------------------------------------------ autotuner
+// For a default class c (the smallest shape covering the chunks), the candidates are every
+// shape whose capacity covers the class's largest vector and is at most 4x the class
+// capacity (warp groups with more chunks per lane, or CTA groups). Each candidate runs 3 + 10
+// batched iterations of 16 synthetic instances (ring plus 7 random out-edges per node, the
+// class's largest n, log utility) in a private engine; the fastest per iteration wins. The
+// choice depends only on the class, so an instance's shape never depends on the mix.
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::pair<int, int>, int> g_tuned;   // (device, default class) -> tuned class
+
+uint64_t splitmix(uint64_t& x) {
+  uint64_t z = (x += 0x9e3779b97f4a7c15ULL);
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+
+mcf_problem* synthetic_problem(int n, uint64_t seed) {
+  const int deg = std::min(8, n - 1);
+  std::vector<int32_t> t, h;
+  for (int i = 0; i < n; ++i) {
+    std::vector<int32_t> used{i, (i + 1) % n};
+    t.push_back(i);
+    h.push_back((i + 1) % n);
+    while ((int)used.size() < deg + 1) {
+      const int j = (int)(splitmix(seed) % (uint64_t)n);
+      if (std::find(used.begin(), used.end(), j) != used.end()) continue;
+      used.push_back(j);
+      t.push_back(i);
+      h.push_back(j);
+    }
+  }
+  const int m = (int)t.size();
+  std::vector<double> cap(m), w((size_t)n * n, 1.0);
+  for (int l = 0; l < m; ++l) cap[l] = 1.0 + 9.0 * (double)(splitmix(seed) >> 11) / 9007199254740992.0;
+  for (auto& x : w) x = 0.5 + (double)(splitmix(seed) >> 11) / 9007199254740992.0;
+  mcf_problem* p = nullptr;
+  mcf_create_problem(n, m, t.data(), h.data(), cap.data(), MCF_LOG, w.data(), nullptr, 0, &p);
+  return p;
+}
+
+int tune_class(int device, int c0) {
+  const int cap0 = kShapes[c0].group * kShapes[c0].vpt;
+  const int n = std::max(4, cap0 * 4 - 8);
+  std::vector<int> cands;
+  for (int s = 0; s < NUM_SHAPES; ++s) {
+    const int cap = kShapes[s].group * kShapes[s].vpt;
+    if (cap >= cap0 && cap <= 4 * cap0) cands.push_back(s);
+  }
+  constexpr int kCount = 16;
+  std::vector<mcf_problem*> probs;
+  for (int i = 0; i < kCount; ++i) probs.push_back(synthetic_problem(n, 1000003ULL * (i + 1)));
+  mcf_options o;
+  mcf_options_default(&o);
+  o.stop_mode = MCF_STOP_NONE;
+  o.max_iters = 1 << 30;
+  o.device = device;
+  int best = c0;
+  double best_t = 1e300;
+  for (int c : cands) {
+    BatchEngine eng(device, kCount);
+    if (eng.init() != MCF_OK) break;
+    bool ok = true;
+    for (int i = 0; i < kCount && ok; ++i) {
+      int slot = 0;
+      ok = probs[i] && eng.add(probs[i], o, nullptr, &slot, c) == MCF_OK;
+    }
+    if (!ok || eng.step(3) != MCF_OK) continue;
+    const auto t0 = std::chrono::steady_clock::now();
+    if (eng.step(10) != MCF_OK) continue;
+    const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (dt < best_t) { best_t = dt; best = c; }
+  }
+  for (mcf_problem* p : probs) mcf_destroy_problem(p);
+  return best;
+}
+}  // namespace
+
+int batch_class_for(int device, int nchunks, bool autotune) {
+  const int c0 = pick_shape(nchunks);
+  if (c0 < 0 || !autotune) return c0;
+  {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    auto it = g_tuned.find({device, c0});
+    if (it != g_tuned.end()) return it->second;
+  }
+  const int c = tune_class(device, c0);
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  g_tuned.emplace(std::make_pair(device, c0), c);
+  return g_tuned[{device, c0}];
 }
 
 }  // namespace pdmcf
@@ -420,7 +519,11 @@ extern "C" int mcf_solve_batch(mcf_problem** probs, int count, const mcf_options
       }
     locks.emplace_back(probs[i]->lock);
     int slot = 0;
-    rc = eng.add(probs[i], *opts, nullptr, &slot);
+    const int nchunks = ((probs[i]->n + 7) / 8 * 8) / 4;
+    const int cls = opts->shape >= 0 && opts->shape < NUM_SHAPES
+                        ? opts->shape
+                        : batch_class_for(opts->device, nchunks, opts->autotune != 0);
+    rc = eng.add(probs[i], *opts, nullptr, &slot, cls);
     if (rc != MCF_OK) return rc;
   }
   const int chunk = std::max(1, std::min(opts->k_check, 50));

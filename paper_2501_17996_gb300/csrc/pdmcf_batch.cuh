@@ -44,6 +44,7 @@ struct BatchInst {
   const float* Gm;
   float* F[2];
   float* Y[2];
+  __nv_bfloat16* Ylo[2];   // compensated-dual tails (nullptr: plain Y)
   float* Pm;
   float* mu;
   float* That;
@@ -113,12 +114,21 @@ batch_edge_kernel(const BatchInst* __restrict__ insts, BatchClassDev cls) {
     for (int v = 0; v < VPT; ++v) {
       const int ci = v * GROUP + lane;
       if (ci < nchunks) {
-        P a1[VW], a2[VW];
+        P a1[VW], a2[VW], dl[VW];
         ld_plain<P, VW>(fo + ci * VW, f[v]);
         ld_plain<P, VW>(yh + ci * VW, a1);
         ld_plain<P, VW>(yt + ci * VW, a2);
 #pragma unroll
-        for (int u = 0; u < VW; ++u) q[v][u] = f[v][u] + alpha * (a1[u] - a2[u]);
+        for (int u = 0; u < VW; ++u) dl[u] = P(0);
+        if (I.Ylo[par]) {
+          float l1[VW], l2[VW];
+          ld_lo<VW>(I.Ylo[par] + (size_t)h * I.ld + ci * VW, l1);
+          ld_lo<VW>(I.Ylo[par] + (size_t)t * I.ld + ci * VW, l2);
+#pragma unroll
+          for (int u = 0; u < VW; ++u) dl[u] = l1[u] - l2[u];
+        }
+#pragma unroll
+        for (int u = 0; u < VW; ++u) q[v][u] = f[v][u] + alpha * ((a1[u] - a2[u]) + dl[u]);
       } else {
 #pragma unroll
         for (int u = 0; u < VW; ++u) { f[v][u] = P(0); q[v][u] = P(0); }
@@ -136,7 +146,7 @@ batch_edge_kernel(const BatchInst* __restrict__ insts, BatchClassDev cls) {
         for (int u = 0; u < VW; ++u) {
           const P fh = q[v][u] > mu ? q[v][u] - mu : P(0);
           out[u] = rho * fh + (P(1) - rho) * f[v][u];
-          const P d = out[u] - f[v][u];
+          const P d = rho * (fh - f[v][u]);   // the step itself, not the rounded difference
           dloc = fma(d, d, dloc);
         }
         st_plain<P, VW>(fn + ci * VW, out);
@@ -212,7 +222,7 @@ batch_node_kernel(const BatchInst* __restrict__ insts, BatchClassDev cls) {
     for (int v = 0; v < VPT; ++v) {
       const int ci = v * GROUP + lane;
       if (ci >= nchunks) continue;
-      P po[VW], yo[VW], wv[VW], gv[VW], yn[VW], that_v[VW], up_v[VW], yh_v[VW];
+      P po[VW], yo[VW], wv[VW], gv[VW], yn[VW], that_v[VW], up_v[VW], yh_v[VW], yl[VW];
       ld_plain<P, VW>(prow + ci * VW, po);
       ld_plain<P, VW>(yrow + ci * VW, yo);
       ld_plain<P, VW>(wrow + ci * VW, wv);
@@ -222,18 +232,28 @@ batch_node_kernel(const BatchInst* __restrict__ insts, BatchClassDev cls) {
         for (int u = 0; u < VW; ++u) gv[u] = I.gamma;
       }
 #pragma unroll
+      for (int u = 0; u < VW; ++u) yl[u] = P(0);
+      if (I.Ylo[par]) ld_lo<VW>(I.Ylo[par] + (size_t)j * I.ld + ci * VW, yl);
+#pragma unroll
       for (int u = 0; u < VW; ++u) {
         const int i = ci * VW + u;
         const P fhat_at = (s[v][u] - (P(1) - rho) * po[u]) * inv_rho;
         const P fplus_at = P(2) * fhat_at - po[u];
         const bool live = (i < I.n) && (i != j);
-        P yhat = P(0);
+        P delta, tr = P(0);
         if (live) {
-          const P vv = yo[u] - beta * fplus_at;
-          yhat = I.kind == 0 ? prox_log<P>(vv, beta, wv[u]) : prox_pow<P>(vv, beta, wv[u], gv[u]);
+          const P vv = yo[u] + (yl[u] - beta * fplus_at);
+          tr = prox_traffic<P>(I.kind, vv, beta, wv[u], gv[u]);
+          delta = -beta * (fplus_at + tr);
+        } else {
+          delta = -(yo[u] + yl[u]);
         }
-        yn[u] = rho * yhat + (P(1) - rho) * yo[u];
-        const P dy = yn[u] - yo[u];
+        const P yhat = live ? (yo[u] + (yl[u] + delta)) : P(0);
+        P hi = yo[u], lo = yl[u];
+        add_split(hi, lo, rho * delta);
+        yn[u] = hi;
+        yl[u] = lo;
+        const P dy = rho * delta;
         loc[0] = fma(dy, dy, loc[0]);
         const P th = -fhat_at;
         that_v[u] = i < I.n ? th : P(0);
@@ -247,7 +267,7 @@ batch_node_kernel(const BatchInst* __restrict__ insts, BatchClassDev cls) {
           }
           if (yhat < P(0)) {
             loc[3] += util_conj_neg<P>(I.kind, yhat, wv[u], gv[u]);
-            const P dt = util_traffic<P>(I.kind, yhat, wv[u], gv[u]) - th;
+            const P dt = tr - th;
             loc[4] = fma(dt, dt, loc[4]);
           } else {
             loc[6] += P(1);
@@ -255,6 +275,7 @@ batch_node_kernel(const BatchInst* __restrict__ insts, BatchClassDev cls) {
           loc[5] = fma(th, th, loc[5]);
         }
       }
+      if (I.Ylo[par ^ 1]) st_lo<VW>(I.Ylo[par ^ 1] + (size_t)j * I.ld + ci * VW, yl);
       st_plain<P, VW>(I.Y[par ^ 1] + (size_t)j * I.ld + ci * VW, yn);
       st_plain<P, VW>(prow + ci * VW, s[v]);
       if (check) {
@@ -314,11 +335,21 @@ batch_check_kernel(const BatchInst* __restrict__ insts, BatchClassDev cls) {
       ld_plain<P, VW>(I.Uprime + to + ci * VW, g2);
       ld_plain<P, VW>(I.Yhat + ho + ci * VW, z1);
       ld_plain<P, VW>(I.Yhat + to + ci * VW, z2);
+      P dl[VW];
+#pragma unroll
+      for (int u = 0; u < VW; ++u) dl[u] = P(0);
+      if (I.Ylo[par]) {
+        float l1[VW], l2[VW];
+        ld_lo<VW>(I.Ylo[par] + ho + ci * VW, l1);
+        ld_lo<VW>(I.Ylo[par] + to + ci * VW, l2);
+#pragma unroll
+        for (int u = 0; u < VW; ++u) dl[u] = l1[u] - l2[u];
+      }
 #pragma unroll
       for (int u = 0; u < VW; ++u) {
         const int i = ci * VW + u;
         if (i >= I.n) continue;
-        const P q = fs[u] + alpha * (y1[u] - y2[u]);
+        const P q = fs[u] + alpha * ((y1[u] - y2[u]) + dl[u]);
         const P fh = q > mu ? q - mu : P(0);
         const P d = fh - q;
         const P gg = g1[u] - g2[u];

@@ -48,7 +48,7 @@ class BatchEngine {
   int free_slots() const;
   int active_count() const;
   // Admit an FP32 request: allocates/initialises the instance state (cold or warm).
-  int add(mcf_problem* p, const mcf_options& o, void* tag, int* slot_out);
+  int add(mcf_problem* p, const mcf_options& o, void* tag, int* slot_out, int cls = -1);
   // Run `iters` batched iterations (graph-captured), then refresh the host scalar mirror
   // and mark instances whose stop rule fired as finished.
   int step(int iters);
@@ -87,6 +87,9 @@ class BatchEngine {
   std::vector<int> finished_;
 };
 
-int batch_admit_shape(const mcf_problem* p);   // shape class an FP32 instance runs in
+int batch_admit_shape(const mcf_problem* p);   // default shape class of an FP32 instance
+// Shape class the batched engine uses for an instance with this many 16-byte chunks per
+// vector: the default class, or the autotuned choice once tuning has run for it.
+int batch_class_for(int device, int nchunks, bool autotune);
 
 }  // namespace pdmcf

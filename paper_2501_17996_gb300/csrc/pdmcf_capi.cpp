@@ -157,6 +157,8 @@ void mcf_options_default(mcf_options* o) {
   o->cuda_stream = nullptr;
   o->omega0 = 1.0;       // Sec. 2.5
   o->stall_checks = 20;
+  o->compensated_duals = 1;
+  o->autotune = 1;
   o->shape = -1;
 }
 
@@ -274,6 +276,47 @@ static int solve_common(mcf_problem* p, const mcf_options* opts, mcf_result* res
   res->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (rc == MCF_OK || rc == MCF_ERR_NOT_CONVERGED || rc == MCF_ERR_NUMERIC) res->status = rc;
   return rc;
+}
+
+int mcf_autotune(mcf_problem* p, const mcf_options* opts, int* best_shape, double* ms_per_iter) {
+  if (!p || !best_shape) return fail(MCF_ERR_INVALID, "problem or best_shape is NULL");
+  int rc = validate_options(opts);
+  if (rc != MCF_OK) return rc;
+  std::lock_guard<std::mutex> g(p->lock);
+  const int vw = opts->precision == MCF_FP64 ? 2 : (opts->precision == MCF_BF16_F ? 8 : 4);
+  const int nchunks = ((p->n + 7) / 8 * 8) / vw;
+  int group[64], vpt[64], pipelined[64];
+  const int count = mcf_shape_info(group, vpt, nullptr, pipelined);
+  int cap0 = 0;
+  for (int s = 0; s < count; ++s)
+    if (!pipelined[s] && group[s] * vpt[s] >= nchunks && (cap0 == 0 || group[s] * vpt[s] < cap0))
+      cap0 = group[s] * vpt[s];
+  int best = -1;
+  double best_ms = 1e300;
+  for (int s = 0; s < count; ++s) {
+    const int cap = group[s] * vpt[s];
+    if (cap < nchunks) continue;
+    if (pipelined[s] ? opts->precision == MCF_FP64 : cap > 4 * cap0) continue;
+    mcf_options o = *opts;
+    o.shape = s;
+    o.stop_mode = MCF_STOP_NONE;
+    o.warm_start = 0;
+    o.max_iters = 3;
+    mcf_result r{};
+    if (device_solve(p, &o, &r) != MCF_OK) continue;
+    o.warm_start = 1;
+    o.max_iters = 10;
+    o.k_check = 10;
+    mcf_kernel_times kt{};
+    if (device_solve(p, &o, &r, &kt) != MCF_OK) continue;
+    const double ms = kt.ms_total / 10.0;
+    if (ms < best_ms) { best_ms = ms; best = s; }
+  }
+  device_free(p);   // tuning iterates are not a resident solution
+  if (best < 0) return fail(MCF_ERR_INVALID, "no launch shape ran for this problem");
+  *best_shape = best;
+  if (ms_per_iter) *ms_per_iter = best_ms;
+  return MCF_OK;
 }
 
 int mcf_solve(mcf_problem* p, const mcf_options* opts, mcf_result* res) {

@@ -35,6 +35,8 @@
 #include <stdint.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "pdmcf_types.h"
 
 namespace pdmcf {
@@ -321,6 +323,68 @@ __device__ __forceinline__ P util_traffic(int kind, P y, P w, P g) {
   return pow(w * g / (-y), P(1) / (P(1) - g));
 }
 
+
+// ------------------------------------------------------------------ compensated duals
+// Y is stored as an FP32 head plus a BF16 tail (Y = hi + lo), which holds the rounding error
+// of the head: edge differences Y_{:,h} - Y_{:,t} are formed as (hi_h - hi_t) + (lo_h - lo_t)
+// and the dual update is applied in increment form, so FP32 iterates are not limited by the
+// FP32 spacing of the (large) dual values.
+
+template <int N>
+__device__ __forceinline__ void ld_lo(const __nv_bfloat16* p, float (&v)[N]) {
+  static_assert(N == 2 || N == 4 || N == 8, "lo chunk");
+  if constexpr (N == 8) {
+    uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
+    const __nv_bfloat16* b = reinterpret_cast<const __nv_bfloat16*>(&u);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = __bfloat162float(b[k]);
+  } else if constexpr (N == 4) {
+    uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+    const __nv_bfloat16* b = reinterpret_cast<const __nv_bfloat16*>(&u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = __bfloat162float(b[k]);
+  } else {
+    unsigned u = __ldg(reinterpret_cast<const unsigned*>(p));
+    const __nv_bfloat16* b = reinterpret_cast<const __nv_bfloat16*>(&u);
+    v[0] = __bfloat162float(b[0]);
+    v[1] = __bfloat162float(b[1]);
+  }
+}
+
+template <int N>
+__device__ __forceinline__ void st_lo(__nv_bfloat16* p, const float (&v)[N]) {
+  __nv_bfloat16 b[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) b[k] = __float2bfloat16_rn(v[k]);
+  if constexpr (N == 8) *reinterpret_cast<uint4*>(p) = *reinterpret_cast<const uint4*>(b);
+  else if constexpr (N == 4) *reinterpret_cast<uint2*>(p) = *reinterpret_cast<const uint2*>(b);
+  else *reinterpret_cast<unsigned*>(p) = *reinterpret_cast<const unsigned*>(b);
+}
+
+// hi + lo + x as a new (hi, lo): Fast2Sum (|hi| >= |lo + x| holds for the tails used here;
+// when hi = 0 the sum is exact anyway).
+template <typename P>
+__device__ __forceinline__ void add_split(P& hi, P& lo, P x) {
+  const P t = lo + x;
+  const P s = hi + t;
+  lo = (hi - s) + t;
+  hi = s;
+}
+
+// t = T(Y^), the traffic of the prox output Y^ = prox_{beta(-u)^*}(v) = v - beta t
+// (Moreau's identity): for log utility t = (v + sqrt(v^2 + 4 beta w)) / (2 beta), evaluated
+// as 2w / (sqrt(v^2 + 4 beta w) - v) when v <= 0; for power utility t = (u')^{-1}(-Y^) from
+// the dual root. Both are small traffic-scale numbers with relative accuracy ~ulp.
+template <typename P>
+__device__ __forceinline__ P prox_traffic(int kind, P v, P beta, P w, P g) {
+  if (kind == 0) {
+    const P s = sqrt(fma(v, v, P(4) * beta * w));
+    return v <= P(0) ? (P(2) * w) / (s - v) : (v + s) / (P(2) * beta);
+  }
+  const P z = prox_pow<P>(v, beta, w, g);
+  return util_traffic<P>(kind, z, w, g);
+}
+
 // ------------------------------------------------------------------ scalar tail
 
 // Deterministic sum of base[b*stride + field] over b < nb by 256 threads: contiguous
@@ -404,6 +468,7 @@ struct IterArgs {
   const P* cap;
   S* F[2];
   P* Y[2];
+  __nv_bfloat16* Ylo[2];  // tails of the compensated duals (nullptr: plain Y)
   P* Pm;
   const P* W;
   const P* Gm;        // per-pair gamma (n x ld) or nullptr
@@ -495,6 +560,7 @@ edge_kernel(IterArgs<P, S> a) {
   const S* __restrict__ Fo = a.F[a.parity];
   S* __restrict__ Fn = a.F[a.parity ^ 1];
   const P* __restrict__ Y = a.Y[a.parity];
+  const __nv_bfloat16* __restrict__ ylo = a.Ylo[a.parity];
   double dsum = 0.0;
 
   int nh = 0, nt = 0;
@@ -522,10 +588,22 @@ edge_kernel(IterArgs<P, S> a) {
         ld_stream<S, VW>(fo + ci * VW, fs);
         ld_keep<P, VW>(yh + ci * VW, a1);
         ld_keep<P, VW>(yt + ci * VW, a2);
+        P dl[VW];
+#pragma unroll
+        for (int u = 0; u < VW; ++u) dl[u] = P(0);
+        if constexpr (std::is_same<P, float>::value) {
+          if (ylo) {
+            float l1[VW], l2[VW];
+            ld_lo<VW>(ylo + (size_t)h * a.ld + ci * VW, l1);
+            ld_lo<VW>(ylo + (size_t)t * a.ld + ci * VW, l2);
+#pragma unroll
+            for (int u = 0; u < VW; ++u) dl[u] = l1[u] - l2[u];
+          }
+        }
 #pragma unroll
         for (int u = 0; u < VW; ++u) {
           f[v][u] = to_p<P>(fs[u]);
-          q[v][u] = f[v][u] + alpha * (a1[u] - a2[u]);
+          q[v][u] = f[v][u] + alpha * ((a1[u] - a2[u]) + dl[u]);
         }
       } else {
 #pragma unroll
@@ -544,7 +622,10 @@ edge_kernel(IterArgs<P, S> a) {
           const P fh = q[v][u] > mu ? q[v][u] - mu : P(0);
           const P fnew = rho * fh + (P(1) - rho) * f[v][u];
           out[u] = from_p<S, P>(fnew);
-          const P d = to_p<P>(out[u]) - f[v][u];
+          // Delta_F uses the step rho (f^ - f) itself: the rounding of the stored iterate
+          // (about one ulp per entry) would otherwise swamp Delta_F near convergence and
+          // drive the primal weight rule
+          const P d = rho * (fh - f[v][u]);
           dloc = fma(d, d, dloc);
         }
         st_stream<S, VW>(Fn + (size_t)e * a.ld + ci * VW, out);
@@ -654,19 +735,34 @@ node_kernel(IterArgs<P, S> a) {
         for (int u = 0; u < VW; ++u) gv[u] = a.gamma;
       }
       P that_v[VW], up_v[VW], yh_v[VW];
+      P yl[VW];                    // tail of the compensated dual (0 when plain)
+#pragma unroll
+      for (int u = 0; u < VW; ++u) yl[u] = P(0);
+      if constexpr (std::is_same<P, float>::value) {
+        if (a.Ylo[a.parity]) ld_lo<VW>(a.Ylo[a.parity] + (size_t)j * a.ld + ci * VW, yl);
+      }
 #pragma unroll
       for (int u = 0; u < VW; ++u) {
         const int i = ci * VW + u;
         const P fhat_at = (s[v][u] - (P(1) - rho) * po[u]) * inv_rho;   // (F^ A^T)_{ij}
         const P fplus_at = P(2) * fhat_at - po[u];                       // (F^{k+1} A^T)_{ij}
         const bool live = (i < a.n) && (i != j);
-        P yhat = P(0);
+        // Y^ - Y = -beta (F^{k+1}A^T + t), t = T(Y^) (Moreau): the increment is formed from
+        // traffic-scale quantities; Y^ = 0 on the diagonal and in the pads.
+        P delta, tr = P(0);
         if (live) {
-          const P vv = yo[u] - beta * fplus_at;
-          yhat = a.kind == 0 ? prox_log<P>(vv, beta, wv[u]) : prox_pow<P>(vv, beta, wv[u], gv[u]);
+          const P vv = yo[u] + (yl[u] - beta * fplus_at);
+          tr = prox_traffic<P>(a.kind, vv, beta, wv[u], gv[u]);
+          delta = -beta * (fplus_at + tr);
+        } else {
+          delta = -(yo[u] + yl[u]);
         }
-        yn[u] = rho * yhat + (P(1) - rho) * yo[u];
-        const P dy = yn[u] - yo[u];
+        const P yhat = live ? (yo[u] + (yl[u] + delta)) : P(0);
+        P hi = yo[u], lo = yl[u];
+        add_split(hi, lo, rho * delta);                                  // Y + rho (Y^ - Y)
+        yn[u] = hi;
+        yl[u] = lo;
+        const P dy = rho * delta;
         loc[0] = fma(dy, dy, loc[0]);
         const P th = -fhat_at;
         that_v[u] = i < a.n ? th : P(0);
@@ -680,13 +776,16 @@ node_kernel(IterArgs<P, S> a) {
           }
           if (yhat < P(0)) {
             loc[3] += util_conj_neg<P>(a.kind, yhat, wv[u], gv[u]);
-            const P dt = util_traffic<P>(a.kind, yhat, wv[u], gv[u]) - th;
+            const P dt = tr - th;
             loc[4] = fma(dt, dt, loc[4]);
           } else {
             loc[6] += P(1);
           }
           loc[5] = fma(th, th, loc[5]);
         }
+      }
+      if constexpr (std::is_same<P, float>::value) {
+        if (a.Ylo[a.parity ^ 1]) st_lo<VW>(a.Ylo[a.parity ^ 1] + (size_t)j * a.ld + ci * VW, yl);
       }
       st_plain<P, VW>(Yn + (size_t)j * a.ld + ci * VW, yn);
       st_plain<P, VW>(prow + ci * VW, s[v]);
@@ -753,6 +852,7 @@ edge_tma_kernel(IterArgs<float, S> a) {
   }
   double dsum = 0.0;
   int cur_h = -1;
+  const __nv_bfloat16* __restrict__ ylo = a.Ylo[a.parity];
   P yh[VPT][VW], sin_[VPT][VW];
 #pragma unroll
   for (int v = 0; v < VPT; ++v)
@@ -784,7 +884,15 @@ edge_tma_kernel(IterArgs<float, S> a) {
 #pragma unroll
       for (int v = 0; v < VPT; ++v) {
         const int ci = v * BLOCK + tid;
-        if (ci < nchunks) ld_keep<P, VW>(yr + ci * VW, yh[v]);
+        if (ci < nchunks) {
+          ld_keep<P, VW>(yr + ci * VW, yh[v]);
+          if (ylo) {   // fold the head's tail in: only differences of Y are used here
+            float l[VW];
+            ld_lo<VW>(ylo + (size_t)h * a.ld + ci * VW, l);
+#pragma unroll
+            for (int u = 0; u < VW; ++u) yh[v][u] += l[u];
+          }
+        }
 #pragma unroll
         for (int u = 0; u < VW; ++u) sin_[v][u] = P(0);
       }
@@ -809,6 +917,12 @@ edge_tma_kernel(IterArgs<float, S> a) {
         P yt[VW];
         ld_plain<S, VW>(sF[st] + ci * VW, fs);
         ld_plain<P, VW>(sY[st] + ci * VW, yt);
+        if (ylo) {
+          float l[VW];
+          ld_lo<VW>(ylo + (size_t)a.e_tail[e] * a.ld + ci * VW, l);
+#pragma unroll
+          for (int u = 0; u < VW; ++u) yt[u] += l[u];
+        }
 #pragma unroll
         for (int u = 0; u < VW; ++u) {
           f[v][u] = to_p<P>(fs[u]);
@@ -837,7 +951,7 @@ edge_tma_kernel(IterArgs<float, S> a) {
           out[u] = from_p<S, P>(rho * fh + (P(1) - rho) * f[v][u]);
           const P fnew = to_p<P>(out[u]);
           sin_[v][u] += fnew;
-          const P d = fnew - f[v][u];
+          const P d = rho * (fh - f[v][u]);   // the step itself (see edge_kernel)
           dloc = fma(d, d, dloc);
         }
         st_stream<S, VW>(Fn + (size_t)e * a.ld + ci * VW, out);
@@ -854,6 +968,140 @@ edge_tma_kernel(IterArgs<float, S> a) {
       if (ci < nchunks) st_plain<P, VW>(pr + ci * VW, sin_[v]);
     }
   }
+  double v1[1] = {dsum};
+  block_sum_write<BLOCK, 1>(v1, a.part_edge + blockIdx.x);
+}
+
+
+// ------------------------------------------------------------------ edge phase with in-sums
+// The register edge phase over head-aligned contiguous edge ranges (one range per CTA, two
+// CTAs per SM): Y_{:,head} and the running in-sum of F^{k+1/2} live in this thread's slices
+// of shared memory (each thread touches only its own chunk positions, so no barriers are
+// added), and the in-sum is written to Pin[head] when the head changes, so the node phase
+// gathers only out-edges.
+template <typename P, typename S, int VPT, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 2)
+edge_insum_kernel(IterArgs<P, S> a) {
+  constexpr int VW = StoreTraits<S>::VW;
+  extern __shared__ __align__(16) unsigned char dyn_is[];
+  P* yh_s = reinterpret_cast<P*>(dyn_is);
+  P* sin_s = yh_s + a.ld;
+  __shared__ GroupScratch<BLOCK> sh;
+  int phase = 0;
+  const int tid = threadIdx.x;
+  const int nchunks = a.ld / VW;
+  const P alpha = (P)a.sc->alpha;
+  const P rho = a.rho;
+  const S* __restrict__ Fo = a.F[a.parity];
+  S* __restrict__ Fn = a.F[a.parity ^ 1];
+  const P* __restrict__ Y = a.Y[a.parity];
+  const __nv_bfloat16* __restrict__ ylo = a.Ylo[a.parity];
+  const int e0 = a.cta_ptr[blockIdx.x], e1 = a.cta_ptr[blockIdx.x + 1];
+  double dsum = 0.0;
+  int cur_h = -1;
+  auto flush = [&](int hh) {
+    P* pr = a.Pin + (size_t)hh * a.ld;
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      const int ci = v * BLOCK + tid;
+      if (ci < nchunks) {
+        P x[VW];
+        ld_plain<P, VW>(sin_s + ci * VW, x);
+        st_plain<P, VW>(pr + ci * VW, x);
+      }
+    }
+  };
+  int nh = 0, nt = 0;
+  P nc = P(0), nmu = P(0);
+  if (e0 < e1) { nh = a.e_head[e0]; nt = a.e_tail[e0]; nc = a.cap[e0]; nmu = a.mu[e0]; }
+  for (int e = e0; e < e1; ++e) {
+    const int h = nh, t = nt;
+    const P c = nc, mu0 = nmu;
+    if (e + 1 < e1) {
+      nh = a.e_head[e + 1];
+      nt = a.e_tail[e + 1];
+      nc = a.cap[e + 1];
+      nmu = a.mu[e + 1];
+    }
+    if (h != cur_h) {   // new head group: flush, then stage Y_{:,h} (head + tail folded in)
+      if (cur_h >= 0) flush(cur_h);
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        const int ci = v * BLOCK + tid;
+        if (ci < nchunks) {
+          P y[VW], z[VW];
+          ld_keep<P, VW>(Y + (size_t)h * a.ld + ci * VW, y);
+          if constexpr (std::is_same<P, float>::value) {
+            if (ylo) {
+              float l[VW];
+              ld_lo<VW>(ylo + (size_t)h * a.ld + ci * VW, l);
+#pragma unroll
+              for (int u = 0; u < VW; ++u) y[u] += l[u];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < VW; ++u) z[u] = P(0);
+          st_plain<P, VW>(yh_s + ci * VW, y);
+          st_plain<P, VW>(sin_s + ci * VW, z);
+        }
+      }
+      cur_h = h;
+    }
+    const S* fo = Fo + (size_t)e * a.ld;
+    const P* yt = Y + (size_t)t * a.ld;
+    P q[VPT][VW], f[VPT][VW];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      const int ci = v * BLOCK + tid;
+      if (ci < nchunks) {
+        S fs[VW];
+        P a1[VW], a2[VW];
+        ld_stream<S, VW>(fo + ci * VW, fs);
+        ld_plain<P, VW>(yh_s + ci * VW, a1);
+        ld_keep<P, VW>(yt + ci * VW, a2);
+        if constexpr (std::is_same<P, float>::value) {
+          if (ylo) {
+            float l[VW];
+            ld_lo<VW>(ylo + (size_t)t * a.ld + ci * VW, l);
+#pragma unroll
+            for (int u = 0; u < VW; ++u) a2[u] += l[u];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < VW; ++u) {
+          f[v][u] = to_p<P>(fs[u]);
+          q[v][u] = f[v][u] + alpha * (a1[u] - a2[u]);
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < VW; ++u) { f[v][u] = P(0); q[v][u] = P(0); }
+      }
+    }
+    const P mu = project_mu<BLOCK, VPT, VW, P>(q, c, mu0, sh, phase);
+    P dloc = P(0);
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      const int ci = v * BLOCK + tid;
+      if (ci < nchunks) {
+        S out[VW];
+        P acc[VW];
+        ld_plain<P, VW>(sin_s + ci * VW, acc);
+#pragma unroll
+        for (int u = 0; u < VW; ++u) {
+          const P fh = q[v][u] > mu ? q[v][u] - mu : P(0);
+          out[u] = from_p<S, P>(rho * fh + (P(1) - rho) * f[v][u]);
+          acc[u] += to_p<P>(out[u]);
+          const P d = rho * (fh - f[v][u]);   // the step itself (see edge_kernel)
+          dloc = fma(d, d, dloc);
+        }
+        st_stream<S, VW>(Fn + (size_t)e * a.ld + ci * VW, out);
+        st_plain<P, VW>(sin_s + ci * VW, acc);
+      }
+    }
+    dsum += (double)dloc;
+    if (tid == 0) a.mu[e] = mu;
+  }
+  if (cur_h >= 0) flush(cur_h);
   double v1[1] = {dsum};
   block_sum_write<BLOCK, 1>(v1, a.part_edge + blockIdx.x);
 }
@@ -897,11 +1145,23 @@ check_kernel(IterArgs<P, S> a) {
       ld_keep<P, VW>(a.Uprime + to + ci * VW, g2);
       ld_keep<P, VW>(a.Yhat + ho + ci * VW, z1);
       ld_keep<P, VW>(a.Yhat + to + ci * VW, z2);
+      P dl[VW];
+#pragma unroll
+      for (int u = 0; u < VW; ++u) dl[u] = P(0);
+      if constexpr (std::is_same<P, float>::value) {
+        if (a.Ylo[a.parity]) {
+          float l1[VW], l2[VW];
+          ld_lo<VW>(a.Ylo[a.parity] + ho + ci * VW, l1);
+          ld_lo<VW>(a.Ylo[a.parity] + to + ci * VW, l2);
+#pragma unroll
+          for (int u = 0; u < VW; ++u) dl[u] = l1[u] - l2[u];
+        }
+      }
 #pragma unroll
       for (int u = 0; u < VW; ++u) {
         const int i = ci * VW + u;
         if (i >= a.n) continue;
-        const P q = to_p<P>(fs[u]) + alpha * (y1[u] - y2[u]);
+        const P q = to_p<P>(fs[u]) + alpha * ((y1[u] - y2[u]) + dl[u]);
         const P fh = q > mu ? q - mu : P(0);
         const P d = fh - q;
         const P g = g1[u] - g2[u];

@@ -38,6 +38,7 @@ template <typename S>
 struct TmaTable {
   void (*edge[NUM_TMA])(IterArgs<float, S>);
   void (*node[NUM_TMA])(IterArgs<float, S>);
+  void (*insum[NUM_TMA])(IterArgs<float, S>);   // register edge phase with in-sums
 };
 const TmaTable<float>& tma_table_f32();
 const TmaTable<__nv_bfloat16>& tma_table_bf16();
@@ -90,6 +91,7 @@ void fill_tma(TmaTable<S>& t) {
   constexpr int V = kTmaVpt[IDX];
   t.edge[IDX] = edge_tma_kernel<S, V, TMA_BLOCK>;
   t.node[IDX] = node_kernel<float, S, V, TMA_NODE_BLOCK, TMA_NODE_BLOCK, 1, true>;
+  t.insum[IDX] = edge_insum_kernel<float, S, V, TMA_BLOCK>;
 }
 
 // Defined in the pdmcf_kernels_<precision>_<part>.cu translation units (compiled in

@@ -195,7 +195,9 @@ class Server {
       ++resident_;
       g.unlock();
       int slot = -1;
-      const int rc = eng->add(t->p, t->opts, t.get(), &slot);
+      const int nchunks = ((t->p->n + 7) / 8 * 8) / 4;
+      const int cls = batch_class_for(t->opts.device, nchunks, t->opts.autotune != 0);
+      const int rc = eng->add(t->p, t->opts, t.get(), &slot, cls);
       g.lock();
       if (rc != MCF_OK) {
         t->p->lock.unlock();

@@ -74,14 +74,18 @@ __global__ void init_y_kernel(P* Y, int n, int ld) {
 // F^ = (q - mu)_+ with q = F^{k-3/2} + alpha_last (Y^{k-1}_{:,h} - Y^{k-1}_{:,t}): the
 // projected flow the last iteration computed (Algorithm 2.1 returns F^{k-1/2}).
 template <typename P, typename S>
-__global__ void fhat_kernel(const S* Fo, const P* Y, const int32_t* et, const int32_t* eh,
-                            const P* mu, const DevScalars* sc, P* out, int m, int ld) {
+__global__ void fhat_kernel(const S* Fo, const P* Y, const __nv_bfloat16* Ylo, const int32_t* et,
+                            const int32_t* eh, const P* mu, const DevScalars* sc, P* out, int m,
+                            int ld) {
   const P alpha = (P)sc->alpha_last;
   const size_t total = (size_t)m * ld;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
     const int e = (int)(idx / ld), i = (int)(idx % ld);
-    const P q = to_p<P>(Fo[idx]) + alpha * (Y[(size_t)eh[e] * ld + i] - Y[(size_t)et[e] * ld + i]);
+    const size_t ih = (size_t)eh[e] * ld + i, it = (size_t)et[e] * ld + i;
+    P dl = P(0);
+    if (Ylo) dl = (P)(__bfloat162float(Ylo[ih]) - __bfloat162float(Ylo[it]));
+    const P q = to_p<P>(Fo[idx]) + alpha * ((Y[ih] - Y[it]) + dl);
     out[idx] = q > mu[e] ? q - mu[e] : P(0);
   }
 }
@@ -94,6 +98,8 @@ struct DeviceState {
   size_t sbytes = 0, pbytes = 0;
   void* F[2] = {nullptr, nullptr};
   void* Y[2] = {nullptr, nullptr};
+  void* Ylo[2] = {nullptr, nullptr};   // compensated-dual tails (FP32/BF16 iterates)
+  bool lo_live = false;                 // the tails match the resident Y
   void *Pm = nullptr, *W = nullptr, *G = nullptr, *mu = nullptr, *cap = nullptr;
   void *That = nullptr, *Uprime = nullptr, *Yhat = nullptr;
   int32_t *e_tail = nullptr, *e_head = nullptr, *in_ptr = nullptr, *out_ptr = nullptr,
@@ -105,7 +111,7 @@ struct DeviceState {
   int shape = -1, auto_shape = -1, block = 0, grid_edge = 0, grid_node = 0, grid_check = 0;
   int requested_shape = -1;   // mcf_options.shape the grids were configured for
   // pipelined edge phase (tma >= 0): one CTA per SM over head-aligned edge ranges
-  int tma = -1, grid_tma = 0, grid_node_pin = 0;
+  int tma = -1, tma_kind = 0, grid_tma = 0, grid_node_pin = 0;   // kind 1 bulk-copy, 2 in-sum
   size_t tma_smem = 0;
   void* Pin = nullptr;
   int32_t* cta_ptr = nullptr;
@@ -115,6 +121,7 @@ struct DeviceState {
   int graph_len = 0;
   double graph_rho = 0.0;
   cudaStream_t graph_stream = nullptr;
+  bool graph_lo = false;
   bool graphs_broken = false;
 };
 
@@ -154,7 +161,7 @@ static void free_state(DeviceState* d) {
   if (!d) return;
   cudaSetDevice(d->device);
   destroy_graphs(d);
-  void* bufs[] = {d->F[0], d->F[1], d->Y[0], d->Y[1], d->Pm, d->W, d->G, d->mu, d->cap,
+  void* bufs[] = {d->F[0], d->F[1], d->Y[0], d->Y[1], d->Ylo[0], d->Ylo[1], d->Pm, d->W, d->G, d->mu, d->cap,
                   d->That, d->Uprime, d->Yhat, d->e_tail, d->e_head, d->in_ptr,
                   d->out_ptr, d->out_idx, d->part_edge, d->part_node, d->part_check, d->sc,
                   d->Pin, d->cta_ptr};
@@ -177,6 +184,7 @@ int64_t device_bytes(const mcf_problem* p, int precision) {
   const size_t sf = elem_bytes_f(precision), sp = elem_bytes_p(precision);
   size_t b = 2 * m * ld * sf;                       // F ping-pong
   b += 2 * n * ld * sp;                             // Y ping-pong
+  if (precision != MCF_FP64) b += 2 * n * ld * 2;   // compensated-dual tails
   b += (3 + (p->gamma_mat.empty() ? 0 : 1)) * n * ld * sp;   // P, W, [gamma], T^ (+below)
   b += 2 * n * ld * sp;                             // U', Y^
   b += 2 * m * sp + (3 * m + 2 * (n + 1)) * 4;      // mu, cap, incidence
@@ -207,7 +215,7 @@ static int upload_data(mcf_problem* p, DeviceState* d, cudaStream_t st) {
   return MCF_OK;
 }
 
-int mcf_shape_count() { return NUM_SHAPES + NUM_TMA; }
+int mcf_shape_count() { return NUM_SHAPES + 2 * NUM_TMA; }
 
 template <typename S> const TmaTable<S>& get_tma_table();
 template <> const TmaTable<float>& get_tma_table<float>() { return tma_table_f32(); }
@@ -219,32 +227,40 @@ template <typename S>
 static int setup_tma(DeviceState* d, int want) {
   constexpr int VW = StoreTraits<S>::VW;
   const int nchunks = (int)(d->ld / VW);
-  int t = -1;
-  if (want >= NUM_SHAPES) t = want - NUM_SHAPES;
-  if (t < 0) { d->tma = -1; return MCF_OK; }
-  if (kTmaVpt[t] * TMA_BLOCK < nchunks) {
-    set_error("pipelined shape too small for this problem");
-    return MCF_ERR_INVALID;
-  }
   int smem_optin = 0, sms = 0;
   CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d->device));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, d->device));
-  const size_t smem = 2 * (size_t)d->ld * (sizeof(S) + sizeof(float));
+  // kind 1: bulk-copy pipeline, two stages of (F row + Y row), one CTA per SM
+  // kind 2: register edge phase with in-sums, (Y row + in-sum row) per CTA, two CTAs per SM
+  const size_t smem1 = 2 * (size_t)d->ld * (sizeof(S) + sizeof(float));
+  const size_t smem2 = 2 * (size_t)d->ld * sizeof(float);
+  int t = -1, kind = 0;
+  if (want >= NUM_SHAPES + NUM_TMA) { t = want - NUM_SHAPES - NUM_TMA; kind = 2; }
+  else if (want >= NUM_SHAPES) { t = want - NUM_SHAPES; kind = 1; }
+  else if (want < 0 && (size_t)d->ld * sizeof(float) >= 8192 && 2 * (smem2 + 4096) <= (size_t)smem_optin) {
+    for (int c = 0; c < NUM_TMA && t < 0; ++c)
+      if (kTmaVpt[c] * TMA_BLOCK >= nchunks) { t = c; kind = 2; }
+  }
+  if (t < 0) { d->tma = -1; d->tma_kind = 0; d->grid_tma = 0; return MCF_OK; }
+  if (kTmaVpt[t] * TMA_BLOCK < nchunks) {
+    set_error("shape too small for this problem");
+    return MCF_ERR_INVALID;
+  }
+  const size_t smem = kind == 1 ? smem1 : smem2;
   if (smem + 4096 > (size_t)smem_optin) {
-    if (want >= NUM_SHAPES) {
-      set_error("rows too long for the pipelined edge phase's shared-memory stages");
-      return MCF_ERR_INVALID;
-    }
-    d->tma = -1;
-    return MCF_OK;
+    set_error("rows too long for this shape's shared-memory use");
+    return MCF_ERR_INVALID;
   }
   const TmaTable<S>& T = get_tma_table<S>();
-  CK(cudaFuncSetAttribute((const void*)T.edge[t], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int on = 0;
+  const void* ek = kind == 1 ? (const void*)T.edge[t] : (const void*)T.insum[t];
+  CK(cudaFuncSetAttribute(ek, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int on = 0, oe = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&on, (const void*)T.node[t], TMA_NODE_BLOCK, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oe, ek, TMA_BLOCK, smem));
   d->tma = t;
+  d->tma_kind = kind;
   d->tma_smem = smem;
-  d->grid_tma = std::max(1, std::min(sms, d->m));
+  d->grid_tma = std::max(1, std::min(std::max(1, oe) * sms, d->m));
   d->grid_node_pin = std::max(1, std::min(d->n, std::max(1, on) * sms));
   return MCF_OK;
 }
@@ -280,6 +296,7 @@ static int setup_grids(DeviceState* d, int want) {
   d->grid_check = grid(d->m, oc);
   return MCF_OK;
 }
+
 
 static int configure_shape(DeviceState* d, int want) {
   if (d->precision == MCF_FP64) {
@@ -381,6 +398,7 @@ static int alloc_state(mcf_problem* p, int precision, int device, int shape, cud
        A(&d->That, n * ld * d->pbytes) && A(&d->Uprime, n * ld * d->pbytes) &&
        A(&d->Yhat, n * ld * d->pbytes) && A(&d->mu, m * d->pbytes) && A(&d->cap, m * d->pbytes);
   if (ok && !p->gamma_mat.empty()) ok = A(&d->G, n * ld * d->pbytes);
+  if (ok && precision != MCF_FP64) ok = A(&d->Ylo[0], n * ld * 2) && A(&d->Ylo[1], n * ld * 2);
   ok = ok && A((void**)&d->e_tail, m * 4) && A((void**)&d->e_head, m * 4) &&
        A((void**)&d->in_ptr, (n + 1) * 4) && A((void**)&d->out_ptr, (n + 1) * 4) &&
        A((void**)&d->out_idx, m * 4);
@@ -425,7 +443,7 @@ void device_free(mcf_problem* p) {
 // ------------------------------------------------------------------ iteration
 
 template <typename P, typename S>
-static IterArgs<P, S> make_args(DeviceState* d, const mcf_problem* p, double rho) {
+static IterArgs<P, S> make_args(DeviceState* d, const mcf_problem* p, double rho, bool lo) {
   IterArgs<P, S> a{};
   a.n = d->n;
   a.m = d->m;
@@ -440,6 +458,8 @@ static IterArgs<P, S> make_args(DeviceState* d, const mcf_problem* p, double rho
   a.F[1] = (S*)d->F[1];
   a.Y[0] = (P*)d->Y[0];
   a.Y[1] = (P*)d->Y[1];
+  a.Ylo[0] = lo ? (__nv_bfloat16*)d->Ylo[0] : nullptr;
+  a.Ylo[1] = lo ? (__nv_bfloat16*)d->Ylo[1] : nullptr;
   a.Pm = (P*)d->Pm;
   a.W = (const P*)d->W;
   a.Gm = (const P*)d->G;
@@ -466,8 +486,8 @@ static cudaError_t launch_phase(DeviceState* d, void** kargs, int which, cudaStr
     if (d->tma >= 0) {
       const TmaTable<S>& T = get_tma_table<S>();
       if (which == 0)
-        return cudaLaunchKernel((const void*)T.edge[d->tma], dim3(d->grid_tma), dim3(TMA_BLOCK),
-                                kargs, d->tma_smem, st);
+        return cudaLaunchKernel(d->tma_kind == 1 ? (const void*)T.edge[d->tma] : (const void*)T.insum[d->tma],
+                                dim3(d->grid_tma), dim3(TMA_BLOCK), kargs, d->tma_smem, st);
       return cudaLaunchKernel((const void*)T.node[d->tma], dim3(d->grid_node_pin),
                               dim3(TMA_NODE_BLOCK), kargs, 0, st);
     }
@@ -605,6 +625,8 @@ static void fill_scalars(const DevScalars& s, const mcf_problem* p, mcf_result* 
   res->rel_kkt = s.rel_kkt;
   res->nonpos_frac = s.nonpos_frac;
   res->omega = s.omega;
+  res->delta_f = s.dF;
+  res->delta_y = s.dY;
 }
 
 // Extra stop rules of the BF16 phase that precedes an FP32 polish: hand off once the
@@ -655,17 +677,25 @@ static int solve_t(mcf_problem* p, DeviceState* d, const mcf_options* o, mcf_res
   h.m = (int)m;
   CK(cudaMemcpyAsync(d->sc, &h, sizeof(DevScalars), cudaMemcpyHostToDevice, st));
 
-  const IterArgs<P, S> args = make_args<P, S>(d, p, o->rho);
+  const bool lo = o->compensated_duals && d->Ylo[0] != nullptr;
+  if (lo && (!warm || !d->lo_live)) {
+    CK(cudaMemsetAsync(d->Ylo[0], 0, (size_t)n * ld * 2, st));
+    CK(cudaMemsetAsync(d->Ylo[1], 0, (size_t)n * ld * 2, st));
+  }
+  d->lo_live = lo;
+  const IterArgs<P, S> args = make_args<P, S>(d, p, o->rho, lo);
   const int64_t max_iters = o->max_iters;
   const int kc = std::max(1, o->k_check);
   bool use_graphs = o->use_graphs && !d->graphs_broken && kt == nullptr;
   EventPool pool;
   if (kt) std::memset(kt, 0, sizeof(*kt));
-  if (use_graphs && (d->graph_len != kc || d->graph_rho != o->rho || d->graph_stream != st)) {
+  if (use_graphs && (d->graph_len != kc || d->graph_rho != o->rho || d->graph_stream != st ||
+                     d->graph_lo != lo)) {
     destroy_graphs(d);
     d->graph_len = kc;
     d->graph_rho = o->rho;
     d->graph_stream = st;
+    d->graph_lo = lo;
   }
   int parity = d->cur;
   int64_t k = 0;
@@ -767,8 +797,10 @@ static int copy_outputs_t(mcf_problem* p, DeviceState* d, mcf_result* res, cudaS
       return MCF_ERR_OOM;
     }
     const int prev = d->cur ^ 1;   // F^{k-3/2} and Y^{k-1} of the last iteration
-    fhat_kernel<P, S><<<2048, 256, 0, st>>>((const S*)d->F[prev], (const P*)d->Y[prev], d->e_tail,
-                                           d->e_head, (const P*)d->mu, d->sc, tmp, m, (int)ld);
+    fhat_kernel<P, S><<<2048, 256, 0, st>>>((const S*)d->F[prev], (const P*)d->Y[prev],
+                                           d->lo_live ? (const __nv_bfloat16*)d->Ylo[prev] : nullptr,
+                                           d->e_tail, d->e_head, (const P*)d->mu, d->sc, tmp, m,
+                                           (int)ld);
     buf.resize((size_t)m * ld);
     cudaError_t e = cudaMemcpyAsync(buf.data(), tmp, buf.size() * sizeof(P), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -785,16 +817,17 @@ static int copy_outputs_t(mcf_problem* p, DeviceState* d, mcf_result* res, cudaS
 
 }  // namespace pdmcf
 
-extern "C" int mcf_shape_info(int* group, int* vpt, int* block, int* pipelined) {
+extern "C" int mcf_shape_info(int* group, int* vpt, int* block, int* kind) {
   using namespace pdmcf;
-  for (int s = 0; s < NUM_SHAPES + NUM_TMA; ++s) {
-    const bool t = s >= NUM_SHAPES;
-    if (group) group[s] = t ? TMA_BLOCK : kShapes[s].group;
-    if (vpt) vpt[s] = t ? kTmaVpt[s - NUM_SHAPES] : kShapes[s].vpt;
-    if (block) block[s] = t ? TMA_BLOCK : kShapes[s].block;
-    if (pipelined) pipelined[s] = t ? 1 : 0;
+  for (int s = 0; s < NUM_SHAPES + 2 * NUM_TMA; ++s) {
+    const int k = s < NUM_SHAPES ? 0 : (s < NUM_SHAPES + NUM_TMA ? 1 : 2);
+    const int t = k == 0 ? 0 : (s - NUM_SHAPES) % NUM_TMA;
+    if (group) group[s] = k ? TMA_BLOCK : kShapes[s].group;
+    if (vpt) vpt[s] = k ? kTmaVpt[t] : kShapes[s].vpt;
+    if (block) block[s] = k ? TMA_BLOCK : kShapes[s].block;
+    if (kind) kind[s] = k;
   }
-  return NUM_SHAPES + NUM_TMA;
+  return NUM_SHAPES + 2 * NUM_TMA;
 }
 
 namespace pdmcf {
@@ -833,6 +866,8 @@ static int transfer_to_fp32(mcf_problem* p, const mcf_options* o, cudaStream_t s
   if (e == cudaSuccess) e = cudaMemcpyAsync(dst->Y[c], src->Y[c], n * ld * 4, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dst->Pm, src->Pm, n * ld * 4, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dst->mu, src->mu, m * 4, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && src->lo_live)
+    e = cudaMemcpyAsync(dst->Ylo[c], src->Ylo[c], n * ld * 2, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     free_state(dst);
@@ -841,6 +876,7 @@ static int transfer_to_fp32(mcf_problem* p, const mcf_options* o, cudaStream_t s
   }
   dst->cur = c;
   dst->valid = true;
+  dst->lo_live = src->lo_live;
   free_state(src);
   p->ds = dst;
   p->data_dirty = true;
@@ -864,6 +900,12 @@ int batch_prepare_state(mcf_problem* p, const mcf_options* o, cudaStream_t st, b
   }
   *warm = o->warm_start && d->valid;
   const size_t n = d->n, m = d->m, ld = d->ld;
+  const bool lo = o->compensated_duals && d->Ylo[0] != nullptr;
+  if (lo && (!*warm || !d->lo_live)) {
+    CK(cudaMemsetAsync(d->Ylo[0], 0, n * ld * 2, st));
+    CK(cudaMemsetAsync(d->Ylo[1], 0, n * ld * 2, st));
+  }
+  d->lo_live = lo;
   if (!*warm) {
     d->cur = 0;
     CK(cudaMemsetAsync(d->F[0], 0, m * ld * 4, st));
@@ -899,6 +941,8 @@ void batch_state_pointers(mcf_problem* p, BatchInst* bi, int* parity) {
   bi->F[1] = (float*)d->F[1];
   bi->Y[0] = (float*)d->Y[0];
   bi->Y[1] = (float*)d->Y[1];
+  bi->Ylo[0] = d->lo_live ? (__nv_bfloat16*)d->Ylo[0] : nullptr;
+  bi->Ylo[1] = d->lo_live ? (__nv_bfloat16*)d->Ylo[1] : nullptr;
   bi->Pm = (float*)d->Pm;
   bi->mu = (float*)d->mu;
   bi->That = (float*)d->That;

@@ -114,5 +114,5 @@ def test_shape_table(lib):
     shapes = lib.mcf_shape_info()
     assert len(shapes) >= 10
     for g, v, b, t in shapes:
-        assert g in (32, 64, 128, 256, 512, 1024) and b % g == 0 and v >= 1 and t in (0, 1)
-    assert sum(t for *_, t in shapes) >= 1
+        assert g in (32, 64, 128, 256, 512, 1024) and b % g == 0 and v >= 1 and t in (0, 1, 2)
+    assert {t for *_, t in shapes} == {0, 1, 2}

@@ -126,3 +126,21 @@ def test_served_budget_rejects_oversized_request(lib):
             assert ei.value.code == lib.MCF_ERR_OOM_BUDGET
         finally:
             lib.mcf_serving_config(120 * 10**9, 256)
+
+
+def test_batch_autotuned_classes_keep_alone_equal_in_mix(lib):
+    """The autotuned shape of a size class is fixed once per process, so alone-vs-mix
+    identity holds with autotuning on (and results match the untuned run within FP32)."""
+    insts = I.batched(seed=11, count=6)
+    probs = [lib.Problem(i) for i in insts]
+    opts = lib.mcf_options_default(stop_mode="none", max_iters=100, k_check=50, autotune=1)
+    _, mix = lib.mcf_solve_batch(probs, opts, want_T=True)
+    _, alone = lib.mcf_solve_batch([probs[2]], opts, want_T=True)
+    assert np.array_equal(alone[0]["T"], mix[2]["T"])
+    plain = lib.mcf_options_default(stop_mode="none", max_iters=100, k_check=50, autotune=0)
+    _, untuned = lib.mcf_solve_batch(probs, plain, want_T=True)
+    for a, b, inst in zip(mix, untuned, insts):
+        m = off(inst.n)
+        assert np.abs(a["T"][m] - b["T"][m]).max() <= 1e-4 * np.abs(b["T"][m]).max()
+    for p in probs:
+        p.close()

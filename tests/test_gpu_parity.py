@@ -116,8 +116,8 @@ def test_slice_trajectory_fp32(lib):
 
 
 def test_slice_pipelined_shapes_fp32(lib):
-    """Every pipelined (bulk-copy) edge-phase shape on the n = 1000 slice: head groups of
-    several edges, head-aligned CTA ranges, in-sums consumed by the node phase."""
+    """Every bulk-copy pipelined and in-sum edge-phase shape on the n = 1000 slice: head
+    groups of several edges, head-aligned CTA ranges, in-sums consumed by the node phase."""
     inst = I.large_slice(1)
     K = 6
     ref = oracle_k(inst, K)
@@ -304,3 +304,34 @@ def test_large_properties_at_full_size(lib):
     if g["feasible"]:
         assert g["utility"] <= g["dual_bound"] * (1 + 1e-6)
     assert np.isfinite(g["rel_cons"])
+
+
+# ------------------------------------------------------------------ precision features
+
+def test_compensated_duals_lower_the_fp32_floor(lib):
+    """On a low-degree network FP32 duals stall near 1e-4 relative KKT; the FP32 head +
+    BF16 tail representation reaches a lower floor and a more accurate T."""
+    inst = sorted(I.batched(seed=3, count=8), key=lambda i: i.n * i.m)[0]
+    ref = O.pdmcf(inst.n, inst.tail, inst.head, inst.cap, inst.kind, inst.w, inst.gamma,
+                  eps=1e-10, stop_mode="kkt", max_iters=100000, k_check=100)
+    m = off(inst.n)
+    out = {}
+    with lib.Problem(inst) as p:
+        for comp in (0, 1):
+            g = p.solve(stop_mode="none", max_iters=8000, k_check=500, compensated_duals=comp,
+                        want_T=True)
+            out[comp] = (g["rel_kkt"], np.max(np.abs(g["T"][m] - ref.T[m]) / ref.T[m]))
+    assert out[1][0] < 0.6 * out[0][0]
+    assert out[1][1] < out[0][1]
+    assert out[1][0] < 1e-4 and out[1][1] < 1e-4
+
+
+def test_autotune_picks_a_working_shape(lib):
+    inst = I.mid(0)
+    with lib.Problem(inst) as p:
+        shape, ms = p.autotune(stop_mode="none")
+        shapes = lib.mcf_shape_info()
+        assert 0 <= shape < len(shapes) and ms > 0
+        g = p.solve(stop_mode="none", max_iters=30, k_check=10, shape=shape, want_T=True)
+    ref = oracle_k(inst, 30)
+    assert rel_err(g["T"], ref.T, off(inst.n)) < 1e-4
