@@ -98,6 +98,10 @@ typedef struct mcf_options {
   int     shape;             /* kernel launch shape index (-1 = automatic); see
                                 mcf_shape_info. Lets tests and the tuner pick any shape
                                 whose capacity covers the problem                          */
+  double  adapt_guard;       /* stop adapting omega (keep it constant, Sec. 2.4) from the
+                                iteration after a stop test whose relative KKT measure
+                                exceeds adapt_guard x the smallest one of this solve;
+                                0 = adapt throughout (default 10)                          */
 } mcf_options;
 
 /* ---------------------------------------------------------------- results */
@@ -123,6 +127,7 @@ typedef struct mcf_result {
   int     stalled;     /* 1 if the stall rule (mcf_options.stall_checks) ended the solve */
   double  delta_f;     /* Delta_F of the last iteration (Eq. e-primal_weight)           */
   double  delta_y;     /* Delta_Y of the last iteration                                 */
+  int64_t omega_frozen_at; /* iteration from which omega stayed constant (-1: never)     */
   double  seconds;     /* wall time of the call                                        */
 } mcf_result;
 

@@ -299,17 +299,24 @@ class Result:
     Y: np.ndarray                # relaxed iterate Y^k (warm-start state)
     mu: np.ndarray               # projection multipliers of the last iteration
     history: list = field(default_factory=list)
+    omega_frozen_at: int = -1    # iteration from which omega stayed constant (-1: never)
 
 
 def pdmcf(n, tail, head, cap, kind, w, gamma=None, *, eps=1e-6, stop_mode="kkt",
           max_iters=100000, rho=1.9, theta=0.5, k_adapt=100, tau=1e-5,
           omega_freeze_iter=-1, k_check=1, F0=None, Y0=None, omega0=1.0,
-          history=False) -> Result:
+          adapt_guard=10.0, history=False) -> Result:
     """Algorithm 2.1 (PDMCF), float64.
 
     stop_mode: "paper" stops when r^k < n m eps (Sec. 2.5), "kkt" when rel_kkt^k < eps,
     "none" runs exactly max_iters iterations. Initialisation F^{-1/2} = 0,
     Y^0 = I - 1 1^T, omega^0 = 1 (Sec. 2.5) unless a warm start is given.
+
+    omega stops adapting from iteration omega_freeze_iter on, and (adapt_guard > 0) from
+    the iteration after a stop test whose rel_kkt exceeds adapt_guard times the smallest
+    rel_kkt of this run: Sec. 2.4 allows ending the adaptation after some iterations, a
+    constant omega keeping the convergence proof; the guard is the point it is applied at.
+    adapt_guard = 0 is the adaptation without that stop.
     """
     tail = np.asarray(tail, dtype=np.int64)
     head = np.asarray(head, dtype=np.int64)
@@ -327,6 +334,7 @@ def pdmcf(n, tail, head, cap, kind, w, gamma=None, *, eps=1e-6, stop_mode="kkt",
     met = None
     Fhat = Yhat = mu = None
     hist = []
+    best_kkt = math.inf
     status = "max_iters"
     k = 0
     while True:
@@ -360,6 +368,11 @@ def pdmcf(n, tail, head, cap, kind, w, gamma=None, *, eps=1e-6, stop_mode="kkt",
         if (k + 1) % k_check == 0 or k + 1 >= max_iters:
             met = metrics(Fhat, Yhat, Q, A, c, util)
             r = met.r
+            if adapt_guard > 0:
+                if met.rel_kkt > adapt_guard * best_kkt and \
+                        (omega_freeze_iter < 0 or omega_freeze_iter > k + 1):
+                    omega_freeze_iter = k + 1
+                best_kkt = min(best_kkt, met.rel_kkt)
             if history:
                 hist.append(dict(k=k + 1, omega=omega, r=r, rel_kkt=met.rel_kkt,
                                  rel_gap=met.rel_gap, rel_cons=met.rel_cons,
@@ -371,7 +384,7 @@ def pdmcf(n, tail, head, cap, kind, w, gamma=None, *, eps=1e-6, stop_mode="kkt",
         raise ValueError("no iteration performed")
     T = -np.asarray(Fhat @ AT)
     U = util.value(T) if (met is not None and met.feasible) else -math.inf
-    return Result(status, k, Fhat, T, Yhat, U, met, omega, F, Y, mu, hist)
+    return Result(status, k, Fhat, T, Yhat, U, met, omega, F, Y, mu, hist, omega_freeze_iter)
 
 
 def shortest_path_flow(n, tail, head, cap):

@@ -42,7 +42,7 @@ class mcf_options(C.Structure):
         ("precision", C.c_int), ("warm_start", C.c_int), ("polish_iters", C.c_int),
         ("use_graphs", C.c_int), ("device", C.c_int), ("cuda_stream", C.c_void_p),
         ("omega0", C.c_double), ("stall_checks", C.c_int), ("compensated_duals", C.c_int),
-        ("autotune", C.c_int), ("shape", C.c_int),
+        ("autotune", C.c_int), ("shape", C.c_int), ("adapt_guard", C.c_double),
     ]
 
 
@@ -54,7 +54,7 @@ class mcf_result(C.Structure):
         ("r_over_nm", C.c_double), ("rel_gap", C.c_double), ("rel_cons", C.c_double),
         ("rel_stat", C.c_double), ("rel_kkt", C.c_double), ("nonpos_frac", C.c_double),
         ("omega", C.c_double), ("stalled", C.c_int), ("delta_f", C.c_double),
-        ("delta_y", C.c_double), ("seconds", C.c_double),
+        ("delta_y", C.c_double), ("omega_frozen_at", C.c_int64), ("seconds", C.c_double),
     ]
 
 

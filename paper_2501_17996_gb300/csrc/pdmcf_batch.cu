@@ -222,6 +222,8 @@ int BatchEngine::add(mcf_problem* p, const mcf_options& o, void* tag, int* slot_
   d.tau = o.tau;
   d.k_adapt = o.k_adapt > 0 ? o.k_adapt : 1;
   d.freeze = o.omega_freeze_iter;
+  d.guard = o.adapt_guard;
+  d.best_kkt = INFINITY;
   d.r = INFINITY;
   d.rel_kkt = INFINITY;
   d.n = p->n;
@@ -374,6 +376,7 @@ void BatchEngine::release(int s) {
   r.omega = d.omega;
   r.delta_f = d.dF;
   r.delta_y = d.dY;
+  r.omega_frozen_at = (d.freeze >= 0 && d.freeze <= d.k) ? d.freeze : -1;
   r.stalled = h_sc_[s].stalled;
   r.status = sl.status;
   batch_finish_state(sl.p, h_sc_[s].parity, d, stream_);

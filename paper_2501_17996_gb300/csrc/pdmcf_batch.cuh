@@ -46,7 +46,8 @@ struct BatchInst {
   float* Y[2];
   __nv_bfloat16* Ylo[2];   // compensated-dual tails (nullptr: plain Y)
   float* Pm;
-  float* mu;
+  float* mu;               // projection multipliers, hi/lo pair
+  float* mu_lo;
   float* That;
   float* Uprime;
   float* Yhat;
@@ -106,6 +107,7 @@ batch_edge_kernel(const BatchInst* __restrict__ insts, BatchClassDev cls) {
     const P rho = I.rho;
     const int nchunks = I.ld / VW;
     const int h = I.e_head[e], t = I.e_tail[e];
+    const P mu0 = I.mu[e], mu0l = I.mu_lo[e];
     const float* fo = I.F[par] + (size_t)e * I.ld;
     const float* yh = I.Y[par] + (size_t)h * I.ld;
     const float* yt = I.Y[par] + (size_t)t * I.ld;
@@ -128,13 +130,14 @@ batch_edge_kernel(const BatchInst* __restrict__ insts, BatchClassDev cls) {
           for (int u = 0; u < VW; ++u) dl[u] = l1[u] - l2[u];
         }
 #pragma unroll
-        for (int u = 0; u < VW; ++u) q[v][u] = f[v][u] + alpha * ((a1[u] - a2[u]) + dl[u]);
+        for (int u = 0; u < VW; ++u)
+          q[v][u] = shifted_q<P>(f[v][u], a1[u], a2[u], dl[u], alpha, mu0, mu0l);
       } else {
 #pragma unroll
-        for (int u = 0; u < VW; ++u) { f[v][u] = P(0); q[v][u] = P(0); }
+        for (int u = 0; u < VW; ++u) { f[v][u] = P(0); q[v][u] = shifted_floor<P>(mu0, mu0l); }
       }
     }
-    const P mu = project_mu<GROUP, VPT, VW, P>(q, I.cap[e], I.mu[e], sh, phase);
+    const P mu = project_mu<GROUP, VPT, VW, P>(q, I.cap[e], P(0), shifted_floor<P>(mu0, mu0l), sh, phase);
     P dloc = P(0);
     float* fn = I.F[par ^ 1] + (size_t)e * I.ld;
 #pragma unroll
@@ -154,7 +157,10 @@ batch_edge_kernel(const BatchInst* __restrict__ insts, BatchClassDev cls) {
     }
     const double d2 = group_sum_double<GROUP>((double)dloc, sh, phase);
     if (lane == 0) {
-      I.mu[e] = mu;
+      P hi, lo;
+      shifted_mu<P>(mu0, mu0l, mu, hi, lo);
+      I.mu[e] = hi;
+      I.mu_lo[e] = lo;
       I.pe[e] = d2;
     }
   }

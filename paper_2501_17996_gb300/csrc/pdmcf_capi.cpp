@@ -124,6 +124,8 @@ int validate_options(const mcf_options* o) {
   if (o->polish_iters < 0) return fail(MCF_ERR_INVALID, "polish_iters must be >= 0");
   if (o->stall_checks < 0) return fail(MCF_ERR_INVALID, "stall_checks must be >= 0");
   if (o->shape < -1 || o->shape >= mcf_shape_count()) return fail(MCF_ERR_INVALID, "unknown shape");
+  if (!(o->adapt_guard >= 0.0) || !std::isfinite(o->adapt_guard))
+    return fail(MCF_ERR_INVALID, "adapt_guard must be finite and >= 0");
   return MCF_OK;
 }
 
@@ -160,6 +162,7 @@ void mcf_options_default(mcf_options* o) {
   o->compensated_duals = 1;
   o->autotune = 1;
   o->shape = -1;
+  o->adapt_guard = 10.0;
 }
 
 int mcf_create_problem(int32_t n, int32_t m, const int32_t* tail, const int32_t* head,

@@ -443,6 +443,14 @@ static __device__ __forceinline__ void scalar_update(DevScalars* s, double dF2, 
     s->nonpos_frac = nonpos / ((double)s->n * (double)(s->n - 1));
     s->check_k = k + 1;
     if (!isfinite(Psum) && feasible) s->numeric_error = 1;
+    // Sec. 2.4: omega may stop adapting after some iterations (a constant omega keeps the
+    // convergence proof); it stops from the next iteration once the measure has risen
+    // above guard x its smallest value in this solve
+    if (s->guard > 0.0) {
+      if (s->rel_kkt > s->guard * s->best_kkt && (s->freeze < 0 || s->freeze > k + 1))
+        s->freeze = k + 1;
+      if (s->rel_kkt < s->best_kkt) s->best_kkt = s->rel_kkt;
+    }
   }
   // Algorithm 2.1, step 3 (Eq. e-primal_weight)
   s->alpha_last = s->alpha;
@@ -474,7 +482,8 @@ struct IterArgs {
   const P* Gm;        // per-pair gamma (n x ld) or nullptr
   P gamma;            // scalar gamma when Gm == nullptr
   int kind;           // 0 log, 1 power
-  P* mu;
+  P* mu;          // projection multipliers: mu + mu_lo (hi/lo pair), one per edge
+  P* mu_lo;
   P* That;
   P* Uprime;
   P* Yhat;
@@ -491,6 +500,36 @@ struct IterArgs {
 
 // ------------------------------------------------------------------ projection
 
+// Entries of q in the frame shifted by the previous multiplier mu0 = m0 + m0l (a hi/lo pair).
+// On the active set q = f + alpha (y_h - y_t) and mu are both about alpha times the edge's
+// price, far above f^ = (q - mu)_+; subtracting mu0 before the projection (y_h - y_t taken
+// exactly by TwoSum, alpha (y_h - y_t) - m0 rounded once by an FMA) keeps the rounding of f^
+// at the scale of f^ and f rather than of alpha * price. The capped-simplex projection is
+// shift-invariant; its floor mu >= 0 becomes nu >= -m0 for nu = mu - mu0.
+template <typename P>
+__device__ __forceinline__ P shifted_q(P f, P yh, P yt, P dl, P alpha, P m0, P m0l) {
+  const P s = yh - yt;
+  const P bb = s - yh;
+  const P err = (yh - (s - bb)) - (yt + bb);
+  return f + (fma(alpha, s, -m0) + fma(alpha, err + dl, -m0l));
+}
+
+// The floor of nu: -(m0 + m0l) rounded, the value shifted_q gives a zero entry (f = 0,
+// y_h = y_t = 0, e.g. the row padding), which therefore never enters the active set.
+template <typename P>
+__device__ __forceinline__ P shifted_floor(P m0, P m0l) { return -m0 - m0l; }
+
+// mu = mu0 + nu as a hi/lo pair (TwoSum, then renormalised); nu at the floor gives mu = 0.
+template <typename P>
+__device__ __forceinline__ void shifted_mu(P m0, P m0l, P nu, P& hi, P& lo) {
+  if (nu <= shifted_floor<P>(m0, m0l)) { hi = P(0); lo = P(0); return; }
+  const P s = m0 + nu;
+  const P bb = s - m0;
+  const P l = ((m0 - (s - bb)) + (nu - bb)) + m0l;
+  hi = s + l;
+  lo = l - (hi - s);
+}
+
 // Capped-simplex projection of one column (Sec. 2.3): mu = 0 if sum (q)_+ <= c, else the
 // root of phi(mu) = sum_i (q_i - mu)_+ - c. phi is convex, decreasing and piecewise
 // linear, so Newton from a point left of the root, mu' = (sum_{q>mu} q - c)/#{q > mu},
@@ -498,9 +537,9 @@ struct IterArgs {
 // (then mu = (sum_active q - c)/|active|, the value the sorted scan of Sec. 2.6 finds).
 // The previous iteration's mu is the starting point; if it lies right of the root, one
 // Newton step from there lands at or left of the root (tangents of a convex function lie
-// below it).
+// below it). `lo` is the floor of mu: 0 for q itself, -mu0 in the shifted frame above.
 template <int GROUP, int VPT, int VW, typename P>
-__device__ __forceinline__ P project_mu(const P (&q)[VPT][VW], P c, P mu0,
+__device__ __forceinline__ P project_mu(const P (&q)[VPT][VW], P c, P mu0, P lo,
                                         GroupScratch<GROUP>& sh, int& phase) {
   auto eval = [&](P mu, P& s, int& cnt) {
     P ls = 0; int lc = 0;
@@ -512,17 +551,17 @@ __device__ __forceinline__ P project_mu(const P (&q)[VPT][VW], P c, P mu0,
     group_sum_count<GROUP>(ls, lc, sh, phase);
     s = ls; cnt = lc;
   };
-  P mu = mu0 > P(0) ? mu0 : P(0);
+  P mu = mu0 > lo ? mu0 : lo;
   P s; int cnt;
   eval(mu, s, cnt);
   P phi = s - (P)cnt * mu - c;
   if (phi <= P(0)) {
-    if (mu == P(0) || phi == P(0)) return mu;           // mu* = 0, or exactly at the root
-    P mn = cnt > 0 ? (s - c) / (P)cnt : P(0);          // Newton step from the right
-    if (mn <= P(0)) {
-      mu = P(0);
+    if (mu == lo || phi == P(0)) return mu;            // at the floor, or exactly at the root
+    P mn = cnt > 0 ? (s - c) / (P)cnt : lo;            // Newton step from the right
+    if (mn <= lo) {
+      mu = lo;
       eval(mu, s, cnt);
-      if (s - c <= P(0)) return P(0);
+      if (s - (P)cnt * lo - c <= P(0)) return lo;
     } else {
       mu = mn;
       eval(mu, s, cnt);
@@ -564,17 +603,20 @@ edge_kernel(IterArgs<P, S> a) {
   double dsum = 0.0;
 
   int nh = 0, nt = 0;
-  P nc = P(0), nmu = P(0);
-  if (gid < a.m) { nh = a.e_head[gid]; nt = a.e_tail[gid]; nc = a.cap[gid]; nmu = a.mu[gid]; }
+  P nc = P(0), nmu = P(0), nmul = P(0);
+  if (gid < a.m) {
+    nh = a.e_head[gid]; nt = a.e_tail[gid]; nc = a.cap[gid]; nmu = a.mu[gid]; nmul = a.mu_lo[gid];
+  }
   for (int e = gid; e < a.m; e += ngroups) {
     const int h = nh, t = nt;
     const P c = nc;
-    const P mu0 = nmu;
+    const P mu0 = nmu, mu0l = nmul;
     if (e + ngroups < a.m) {   // next edge's indices and scalars, one edge ahead
       nh = a.e_head[e + ngroups];
       nt = a.e_tail[e + ngroups];
       nc = a.cap[e + ngroups];
       nmu = a.mu[e + ngroups];
+      nmul = a.mu_lo[e + ngroups];
     }
     const S* fo = Fo + (size_t)e * a.ld;
     const P* yh = Y + (size_t)h * a.ld;
@@ -603,14 +645,14 @@ edge_kernel(IterArgs<P, S> a) {
 #pragma unroll
         for (int u = 0; u < VW; ++u) {
           f[v][u] = to_p<P>(fs[u]);
-          q[v][u] = f[v][u] + alpha * ((a1[u] - a2[u]) + dl[u]);
+          q[v][u] = shifted_q<P>(f[v][u], a1[u], a2[u], dl[u], alpha, mu0, mu0l);
         }
       } else {
 #pragma unroll
-        for (int u = 0; u < VW; ++u) { f[v][u] = P(0); q[v][u] = P(0); }
+        for (int u = 0; u < VW; ++u) { f[v][u] = P(0); q[v][u] = shifted_floor<P>(mu0, mu0l); }
       }
     }
-    const P mu = project_mu<GROUP, VPT, VW, P>(q, c, mu0, sh, phase);
+    const P mu = project_mu<GROUP, VPT, VW, P>(q, c, P(0), shifted_floor<P>(mu0, mu0l), sh, phase);
     P dloc = P(0);   // this thread's part of ||dF||^2 for this edge; FP64 across edges
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
@@ -632,7 +674,12 @@ edge_kernel(IterArgs<P, S> a) {
       }
     }
     dsum += (double)dloc;
-    if (lane == 0) a.mu[e] = mu;
+    if (lane == 0) {
+      P hi, lo;
+      shifted_mu<P>(mu0, mu0l, mu, hi, lo);
+      a.mu[e] = hi;
+      a.mu_lo[e] = lo;
+    }
   }
   double v1[1] = {dsum};
   block_sum_write<BLOCK, 1>(v1, a.part_edge + blockIdx.x);
@@ -671,12 +718,14 @@ node_kernel(IterArgs<P, S> a) {
     // PIN the edge phase already summed the in-edges into Pin[j].
     const int ib = a.in_ptr[j], nin = PIN ? 0 : a.in_ptr[j + 1] - ib;
     const int ob = a.out_ptr[j], deg = nin + (a.out_ptr[j + 1] - ob);
-    if constexpr (PIN) {
+    if constexpr (PIN) {   // only heads of some edge were written; others sum to zero
       const P* pr = a.Pin + (size_t)j * a.ld;
+      if (a.in_ptr[j + 1] > ib) {
 #pragma unroll
-      for (int v = 0; v < VPT; ++v) {
-        const int ci = v * GROUP + lane;
-        if (ci < nchunks) ld_plain<P, VW>(pr + ci * VW, s[v]);
+        for (int v = 0; v < VPT; ++v) {
+          const int ci = v * GROUP + lane;
+          if (ci < nchunks) ld_plain<P, VW>(pr + ci * VW, s[v]);
+        }
       }
     }
     auto row = [&](int k) -> const S* {
@@ -853,23 +902,25 @@ edge_tma_kernel(IterArgs<float, S> a) {
   double dsum = 0.0;
   int cur_h = -1;
   const __nv_bfloat16* __restrict__ ylo = a.Ylo[a.parity];
-  P yh[VPT][VW], sin_[VPT][VW];
+  P yh[VPT][VW], yhl[VPT][VW], sin_[VPT][VW];   // head's Y (hi, tail) and the in-sum
 #pragma unroll
   for (int v = 0; v < VPT; ++v)
 #pragma unroll
-    for (int u = 0; u < VW; ++u) { yh[v][u] = P(0); sin_[v][u] = P(0); }
+    for (int u = 0; u < VW; ++u) { yh[v][u] = P(0); yhl[v][u] = P(0); sin_[v][u] = P(0); }
   // per-edge scalars of the next edge are fetched one edge ahead (off the critical path)
   int nx_h = cnt > 0 ? a.e_head[e0] : 0;
   P nx_c = cnt > 0 ? a.cap[e0] : P(0), nx_mu = cnt > 0 ? a.mu[e0] : P(0);
+  P nx_mul = cnt > 0 ? a.mu_lo[e0] : P(0);
 
   for (int i = 0; i < cnt; ++i) {
     const int e = e0 + i, st = i & 1;
     const int h = nx_h;
-    const P c_e = nx_c, mu_e = nx_mu;
+    const P c_e = nx_c, mu_e = nx_mu, mu_el = nx_mul;
     if (i + 1 < cnt) {
       nx_h = a.e_head[e + 1];
       nx_c = a.cap[e + 1];
       nx_mu = a.mu[e + 1];
+      nx_mul = a.mu_lo[e + 1];
     }
     if (h != cur_h) {   // new head group: flush the in-sum, fetch Y_{:,h} while we wait
       if (cur_h >= 0) {
@@ -886,12 +937,7 @@ edge_tma_kernel(IterArgs<float, S> a) {
         const int ci = v * BLOCK + tid;
         if (ci < nchunks) {
           ld_keep<P, VW>(yr + ci * VW, yh[v]);
-          if (ylo) {   // fold the head's tail in: only differences of Y are used here
-            float l[VW];
-            ld_lo<VW>(ylo + (size_t)h * a.ld + ci * VW, l);
-#pragma unroll
-            for (int u = 0; u < VW; ++u) yh[v][u] += l[u];
-          }
+          if (ylo) ld_lo<VW>(ylo + (size_t)h * a.ld + ci * VW, yhl[v]);
         }
 #pragma unroll
         for (int u = 0; u < VW; ++u) sin_[v][u] = P(0);
@@ -914,23 +960,25 @@ edge_tma_kernel(IterArgs<float, S> a) {
       const int ci = v * BLOCK + tid;
       if (ci < nchunks) {
         S fs[VW];
-        P yt[VW];
+        P yt[VW], dl[VW];
         ld_plain<S, VW>(sF[st] + ci * VW, fs);
         ld_plain<P, VW>(sY[st] + ci * VW, yt);
+#pragma unroll
+        for (int u = 0; u < VW; ++u) dl[u] = P(0);
         if (ylo) {
           float l[VW];
           ld_lo<VW>(ylo + (size_t)a.e_tail[e] * a.ld + ci * VW, l);
 #pragma unroll
-          for (int u = 0; u < VW; ++u) yt[u] += l[u];
+          for (int u = 0; u < VW; ++u) dl[u] = yhl[v][u] - l[u];
         }
 #pragma unroll
         for (int u = 0; u < VW; ++u) {
           f[v][u] = to_p<P>(fs[u]);
-          q[v][u] = f[v][u] + alpha * (yh[v][u] - yt[u]);
+          q[v][u] = shifted_q<P>(f[v][u], yh[v][u], yt[u], dl[u], alpha, mu_e, mu_el);
         }
       } else {
 #pragma unroll
-        for (int u = 0; u < VW; ++u) { f[v][u] = P(0); q[v][u] = P(0); }
+        for (int u = 0; u < VW; ++u) { f[v][u] = P(0); q[v][u] = shifted_floor<P>(mu_e, mu_el); }
       }
     }
     __syncthreads();   // every thread is done with stage st: refill it with edge i+2
@@ -938,7 +986,7 @@ edge_tma_kernel(IterArgs<float, S> a) {
       fence_proxy_async();
       issue(i + 2);
     }
-    const P mu = project_mu<BLOCK, VPT, VW, P>(q, c_e, mu_e, sh, phase);
+    const P mu = project_mu<BLOCK, VPT, VW, P>(q, c_e, P(0), shifted_floor<P>(mu_e, mu_el), sh, phase);
     P dloc = P(0);
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
@@ -958,7 +1006,12 @@ edge_tma_kernel(IterArgs<float, S> a) {
       }
     }
     dsum += (double)dloc;
-    if (tid == 0) a.mu[e] = mu;
+    if (tid == 0) {
+      P hi, lo;
+      shifted_mu<P>(mu_e, mu_el, mu, hi, lo);
+      a.mu[e] = hi;
+      a.mu_lo[e] = lo;
+    }
   }
   if (cur_h >= 0) {
     P* pr = a.Pin + (size_t)cur_h * a.ld;
@@ -1012,18 +1065,21 @@ edge_insum_kernel(IterArgs<P, S> a) {
     }
   };
   int nh = 0, nt = 0;
-  P nc = P(0), nmu = P(0);
-  if (e0 < e1) { nh = a.e_head[e0]; nt = a.e_tail[e0]; nc = a.cap[e0]; nmu = a.mu[e0]; }
+  P nc = P(0), nmu = P(0), nmul = P(0);
+  if (e0 < e1) {
+    nh = a.e_head[e0]; nt = a.e_tail[e0]; nc = a.cap[e0]; nmu = a.mu[e0]; nmul = a.mu_lo[e0];
+  }
   for (int e = e0; e < e1; ++e) {
     const int h = nh, t = nt;
-    const P c = nc, mu0 = nmu;
+    const P c = nc, mu0 = nmu, mu0l = nmul;
     if (e + 1 < e1) {
       nh = a.e_head[e + 1];
       nt = a.e_tail[e + 1];
       nc = a.cap[e + 1];
       nmu = a.mu[e + 1];
+      nmul = a.mu_lo[e + 1];
     }
-    if (h != cur_h) {   // new head group: flush, then stage Y_{:,h} (head + tail folded in)
+    if (h != cur_h) {   // new head group: flush, then stage Y_{:,h} (its tail stays in L1/L2)
       if (cur_h >= 0) flush(cur_h);
 #pragma unroll
       for (int v = 0; v < VPT; ++v) {
@@ -1031,14 +1087,6 @@ edge_insum_kernel(IterArgs<P, S> a) {
         if (ci < nchunks) {
           P y[VW], z[VW];
           ld_keep<P, VW>(Y + (size_t)h * a.ld + ci * VW, y);
-          if constexpr (std::is_same<P, float>::value) {
-            if (ylo) {
-              float l[VW];
-              ld_lo<VW>(ylo + (size_t)h * a.ld + ci * VW, l);
-#pragma unroll
-              for (int u = 0; u < VW; ++u) y[u] += l[u];
-            }
-          }
 #pragma unroll
           for (int u = 0; u < VW; ++u) z[u] = P(0);
           st_plain<P, VW>(yh_s + ci * VW, y);
@@ -1055,29 +1103,32 @@ edge_insum_kernel(IterArgs<P, S> a) {
       const int ci = v * BLOCK + tid;
       if (ci < nchunks) {
         S fs[VW];
-        P a1[VW], a2[VW];
+        P a1[VW], a2[VW], dl[VW];
         ld_stream<S, VW>(fo + ci * VW, fs);
         ld_plain<P, VW>(yh_s + ci * VW, a1);
         ld_keep<P, VW>(yt + ci * VW, a2);
+#pragma unroll
+        for (int u = 0; u < VW; ++u) dl[u] = P(0);
         if constexpr (std::is_same<P, float>::value) {
           if (ylo) {
-            float l[VW];
-            ld_lo<VW>(ylo + (size_t)t * a.ld + ci * VW, l);
+            float l1[VW], l2[VW];
+            ld_lo<VW>(ylo + (size_t)h * a.ld + ci * VW, l1);
+            ld_lo<VW>(ylo + (size_t)t * a.ld + ci * VW, l2);
 #pragma unroll
-            for (int u = 0; u < VW; ++u) a2[u] += l[u];
+            for (int u = 0; u < VW; ++u) dl[u] = l1[u] - l2[u];
           }
         }
 #pragma unroll
         for (int u = 0; u < VW; ++u) {
           f[v][u] = to_p<P>(fs[u]);
-          q[v][u] = f[v][u] + alpha * (a1[u] - a2[u]);
+          q[v][u] = shifted_q<P>(f[v][u], a1[u], a2[u], dl[u], alpha, mu0, mu0l);
         }
       } else {
 #pragma unroll
-        for (int u = 0; u < VW; ++u) { f[v][u] = P(0); q[v][u] = P(0); }
+        for (int u = 0; u < VW; ++u) { f[v][u] = P(0); q[v][u] = shifted_floor<P>(mu0, mu0l); }
       }
     }
-    const P mu = project_mu<BLOCK, VPT, VW, P>(q, c, mu0, sh, phase);
+    const P mu = project_mu<BLOCK, VPT, VW, P>(q, c, P(0), shifted_floor<P>(mu0, mu0l), sh, phase);
     P dloc = P(0);
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
@@ -1099,7 +1150,12 @@ edge_insum_kernel(IterArgs<P, S> a) {
       }
     }
     dsum += (double)dloc;
-    if (tid == 0) a.mu[e] = mu;
+    if (tid == 0) {
+      P hi, lo;
+      shifted_mu<P>(mu0, mu0l, mu, hi, lo);
+      a.mu[e] = hi;
+      a.mu_lo[e] = lo;
+    }
   }
   if (cur_h >= 0) flush(cur_h);
   double v1[1] = {dsum};
@@ -1223,7 +1279,7 @@ project_kernel(ProjArgs a) {
       }
     }
     const float mu0 = a.mu[e];
-    const float mu = project_mu<GROUP, VPT, VW, float>(q, a.cap[e], mu0 > 0.f ? mu0 : 0.f, sh, phase);
+    const float mu = project_mu<GROUP, VPT, VW, float>(q, a.cap[e], mu0 > 0.f ? mu0 : 0.f, 0.f, sh, phase);
     float dloc = 0.f;
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {

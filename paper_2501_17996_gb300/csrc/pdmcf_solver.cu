@@ -72,11 +72,12 @@ __global__ void init_y_kernel(P* Y, int n, int ld) {
 }
 
 // F^ = (q - mu)_+ with q = F^{k-3/2} + alpha_last (Y^{k-1}_{:,h} - Y^{k-1}_{:,t}): the
-// projected flow the last iteration computed (Algorithm 2.1 returns F^{k-1/2}).
+// projected flow the last iteration computed (Algorithm 2.1 returns F^{k-1/2}), formed in the
+// frame shifted by that iteration's multiplier (hi/lo pair) as the edge phase formed it.
 template <typename P, typename S>
 __global__ void fhat_kernel(const S* Fo, const P* Y, const __nv_bfloat16* Ylo, const int32_t* et,
-                            const int32_t* eh, const P* mu, const DevScalars* sc, P* out, int m,
-                            int ld) {
+                            const int32_t* eh, const P* mu, const P* mu_lo, const DevScalars* sc,
+                            P* out, int m, int ld) {
   const P alpha = (P)sc->alpha_last;
   const size_t total = (size_t)m * ld;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
@@ -85,8 +86,8 @@ __global__ void fhat_kernel(const S* Fo, const P* Y, const __nv_bfloat16* Ylo, c
     const size_t ih = (size_t)eh[e] * ld + i, it = (size_t)et[e] * ld + i;
     P dl = P(0);
     if (Ylo) dl = (P)(__bfloat162float(Ylo[ih]) - __bfloat162float(Ylo[it]));
-    const P q = to_p<P>(Fo[idx]) + alpha * ((Y[ih] - Y[it]) + dl);
-    out[idx] = q > mu[e] ? q - mu[e] : P(0);
+    const P q = shifted_q<P>(to_p<P>(Fo[idx]), Y[ih], Y[it], dl, alpha, mu[e], mu_lo[e]);
+    out[idx] = q > P(0) ? q : P(0);
   }
 }
 
@@ -187,7 +188,7 @@ int64_t device_bytes(const mcf_problem* p, int precision) {
   if (precision != MCF_FP64) b += 2 * n * ld * 2;   // compensated-dual tails
   b += (3 + (p->gamma_mat.empty() ? 0 : 1)) * n * ld * sp;   // P, W, [gamma], T^ (+below)
   b += 2 * n * ld * sp;                             // U', Y^
-  b += 2 * m * sp + (3 * m + 2 * (n + 1)) * 4;      // mu, cap, incidence
+  b += 3 * m * sp + (3 * m + 2 * (n + 1)) * 4;      // mu (hi/lo), cap, incidence
   b += 64 * 1024;                                   // partials, scalars
   return (int64_t)b;
 }
@@ -396,7 +397,7 @@ static int alloc_state(mcf_problem* p, int precision, int device, int shape, cud
   for (int i = 0; i < 2 && ok; ++i) ok = A(&d->F[i], m * ld * d->sbytes) && A(&d->Y[i], n * ld * d->pbytes);
   ok = ok && A(&d->Pm, n * ld * d->pbytes) && A(&d->W, n * ld * d->pbytes) &&
        A(&d->That, n * ld * d->pbytes) && A(&d->Uprime, n * ld * d->pbytes) &&
-       A(&d->Yhat, n * ld * d->pbytes) && A(&d->mu, m * d->pbytes) && A(&d->cap, m * d->pbytes);
+       A(&d->Yhat, n * ld * d->pbytes) && A(&d->mu, 2 * m * d->pbytes) && A(&d->cap, m * d->pbytes);
   if (ok && !p->gamma_mat.empty()) ok = A(&d->G, n * ld * d->pbytes);
   if (ok && precision != MCF_FP64) ok = A(&d->Ylo[0], n * ld * 2) && A(&d->Ylo[1], n * ld * 2);
   ok = ok && A((void**)&d->e_tail, m * 4) && A((void**)&d->e_head, m * 4) &&
@@ -466,6 +467,7 @@ static IterArgs<P, S> make_args(DeviceState* d, const mcf_problem* p, double rho
   a.gamma = (P)p->gamma_scalar;
   a.kind = p->kind;
   a.mu = (P*)d->mu;
+  a.mu_lo = (P*)d->mu + d->m;
   a.That = (P*)d->That;
   a.Uprime = (P*)d->Uprime;
   a.Yhat = (P*)d->Yhat;
@@ -627,6 +629,7 @@ static void fill_scalars(const DevScalars& s, const mcf_problem* p, mcf_result* 
   res->omega = s.omega;
   res->delta_f = s.dF;
   res->delta_y = s.dY;
+  res->omega_frozen_at = (s.freeze >= 0 && s.freeze <= s.k) ? s.freeze : -1;
 }
 
 // Extra stop rules of the BF16 phase that precedes an FP32 polish: hand off once the
@@ -654,7 +657,7 @@ static int solve_t(mcf_problem* p, DeviceState* d, const mcf_options* o, mcf_res
     CK(cudaMemsetAsync(d->F[0], 0, m * ld * d->sbytes, st));
     CK(cudaMemsetAsync(d->F[1], 0, m * ld * d->sbytes, st));
     CK(cudaMemsetAsync(d->Pm, 0, (size_t)n * ld * d->pbytes, st));
-    CK(cudaMemsetAsync(d->mu, 0, m * d->pbytes, st));
+    CK(cudaMemsetAsync(d->mu, 0, 2 * m * d->pbytes, st));
     init_y_kernel<P><<<1024, 256, 0, st>>>((P*)d->Y[0], n, (int)ld);
     CK(cudaGetLastError());
     p->omega = o->omega0 > 0 ? o->omega0 : 1.0;
@@ -671,6 +674,8 @@ static int solve_t(mcf_problem* p, DeviceState* d, const mcf_options* o, mcf_res
   h.tau = o->tau;
   h.k_adapt = o->k_adapt > 0 ? o->k_adapt : 1;
   h.freeze = o->omega_freeze_iter;
+  h.guard = o->adapt_guard;
+  h.best_kkt = INFINITY;
   h.r = INFINITY;
   h.rel_kkt = INFINITY;
   h.n = n;
@@ -799,7 +804,8 @@ static int copy_outputs_t(mcf_problem* p, DeviceState* d, mcf_result* res, cudaS
     const int prev = d->cur ^ 1;   // F^{k-3/2} and Y^{k-1} of the last iteration
     fhat_kernel<P, S><<<2048, 256, 0, st>>>((const S*)d->F[prev], (const P*)d->Y[prev],
                                            d->lo_live ? (const __nv_bfloat16*)d->Ylo[prev] : nullptr,
-                                           d->e_tail, d->e_head, (const P*)d->mu, d->sc, tmp, m,
+                                           d->e_tail, d->e_head, (const P*)d->mu,
+                                           (const P*)d->mu + m, d->sc, tmp, m,
                                            (int)ld);
     buf.resize((size_t)m * ld);
     cudaError_t e = cudaMemcpyAsync(buf.data(), tmp, buf.size() * sizeof(P), cudaMemcpyDeviceToHost, st);
@@ -865,7 +871,7 @@ static int transfer_to_fp32(mcf_problem* p, const mcf_options* o, cudaStream_t s
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(dst->Y[c], src->Y[c], n * ld * 4, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dst->Pm, src->Pm, n * ld * 4, cudaMemcpyDeviceToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(dst->mu, src->mu, m * 4, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dst->mu, src->mu, 2 * m * 4, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess && src->lo_live)
     e = cudaMemcpyAsync(dst->Ylo[c], src->Ylo[c], n * ld * 2, cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -911,7 +917,7 @@ int batch_prepare_state(mcf_problem* p, const mcf_options* o, cudaStream_t st, b
     CK(cudaMemsetAsync(d->F[0], 0, m * ld * 4, st));
     CK(cudaMemsetAsync(d->F[1], 0, m * ld * 4, st));
     CK(cudaMemsetAsync(d->Pm, 0, n * ld * 4, st));
-    CK(cudaMemsetAsync(d->mu, 0, m * 4, st));
+    CK(cudaMemsetAsync(d->mu, 0, 2 * m * 4, st));
     init_y_kernel<float><<<1024, 256, 0, st>>>((float*)d->Y[0], (int)n, (int)ld);
     CK(cudaGetLastError());
     p->omega = o->omega0 > 0 ? o->omega0 : 1.0;
@@ -945,6 +951,7 @@ void batch_state_pointers(mcf_problem* p, BatchInst* bi, int* parity) {
   bi->Ylo[1] = d->lo_live ? (__nv_bfloat16*)d->Ylo[1] : nullptr;
   bi->Pm = (float*)d->Pm;
   bi->mu = (float*)d->mu;
+  bi->mu_lo = (float*)d->mu + d->m;
   bi->That = (float*)d->That;
   bi->Uprime = (float*)d->Uprime;
   bi->Yhat = (float*)d->Yhat;

@@ -17,20 +17,24 @@ from oracle import pdmcf as O  # noqa: E402
 from paper_2501_17996_gb300 import instances as I  # noqa: E402
 
 CASES = {
-    # name: (instance factory, rel_kkt tolerance)
-    "tiny_s0": (lambda: I.tiny(0), 1e-10),
-    "mid_s0": (lambda: I.mid(0), 1e-9),
-    "midpow_s0": (lambda: I.large(0, n=100), 1e-9),
-    "slice_s0": (lambda: I.large_slice(0), 1e-7),
+    # name: (instance factory, rel_kkt tolerance, iterations between stop tests)
+    "tiny_s0": (lambda: I.tiny(0), 1e-10, 10),
+    "mid_s0": (lambda: I.mid(0), 1e-9, 10),
+    "midpow_s0": (lambda: I.large(0, n=100), 1e-9, 10),
+    "slice_s0": (lambda: I.large_slice(0), 1e-7, 10),
+    # stopped at the acceptance tolerance with the stop test every 50 iterations, as the
+    # GPU solves they are compared with
+    "mid_s0_kkt1e-4": (lambda: I.mid(0), 1e-4, 50),
+    "midpow_s0_kkt1e-4": (lambda: I.large(0, n=100), 1e-4, 50),
 }
 
 
 def make(name: str) -> str:
-    factory, tol = CASES[name]
+    factory, tol, k_check = CASES[name]
     inst = factory()
     t0 = time.time()
     r = O.pdmcf(inst.n, inst.tail, inst.head, inst.cap, inst.kind, inst.w, inst.gamma,
-                eps=tol, stop_mode="kkt", max_iters=500000, k_check=10)
+                eps=tol, stop_mode="kkt", max_iters=500000, k_check=k_check)
     path = os.path.join(HERE, f"oracle_{name}.npz")
     np.savez_compressed(path, T=r.T, Yhat=r.Yhat, utility=r.utility, iters=r.iters,
                         rel_kkt=r.metrics.rel_kkt, rel_gap=r.metrics.rel_gap,
@@ -41,5 +45,6 @@ def make(name: str) -> str:
 
 
 if __name__ == "__main__":
-    for name in (sys.argv[1:] or ["tiny_s0", "mid_s0", "midpow_s0"]):
+    for name in (sys.argv[1:] or ["tiny_s0", "mid_s0", "midpow_s0", "mid_s0_kkt1e-4",
+                                  "midpow_s0_kkt1e-4"]):
         make(name)

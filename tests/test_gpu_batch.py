@@ -69,11 +69,14 @@ def test_batch_converged_matches_oracle(lib):
     for r in res:
         assert (r["status"] == lib.MCF_OK and r["rel_kkt"] < 1e-4) or \
             (r["stalled"] == 1 and r["rel_kkt"] < 5e-4)
+    # the acceptance criterion: utility within 1e-4 of the optimum, T within 1e-3 of the
+    # oracle's T stopped the same way (relative KKT 1e-4, stop test every 50 iterations)
     for name, r, inst in (("mid_s0", res[0], insts[0]), ("midpow_s0", res[1], insts[1])):
         g = gold[name]
+        Tref = np.load(os.path.join(GOLDEN, f"oracle_{name}_kkt1e-4.npz"))["T"]
         m = off(inst.n)
         assert abs(r["utility"] - float(g["utility"])) <= 1e-4 * abs(float(g["utility"]))
-        assert np.max(np.abs(r["T"][m] - g["T"][m]) / g["T"][m]) <= 1e-3
+        assert np.max(np.abs(r["T"][m] - Tref[m]) / Tref[m]) <= 1e-3
     for p in probs:
         p.close()
 

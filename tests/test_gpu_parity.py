@@ -84,6 +84,23 @@ def test_fp64_trajectory_matches_oracle(lib, case):
     assert np.all(np.diag(g["Y"]) == 0)
 
 
+def test_adaptation_stop_matches_oracle(lib):
+    """The stop of the omega adaptation (Sec. 2.4) is taken on the device at the same check
+    as in the oracle, and the FP64 trajectories agree past it."""
+    inst = I.mid(0)
+    K = 1500
+    ref = O.pdmcf(inst.n, inst.tail, inst.head, inst.cap, inst.kind, inst.w, inst.gamma,
+                  stop_mode="none", max_iters=K, k_check=50, adapt_guard=1.05)
+    assert ref.omega_frozen_at > 0
+    with lib.Problem(inst) as p:
+        g = p.solve(precision="fp64", stop_mode="none", max_iters=K, k_check=50,
+                    adapt_guard=1.05, want_T=True)
+    m = off(inst.n)
+    assert g["omega_frozen_at"] == ref.omega_frozen_at
+    assert g["omega"] == pytest.approx(ref.omega, rel=1e-9)
+    assert rel_err(g["T"], ref.T, m) < 1e-7
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_every_shape_matches_oracle(lib, precision):
     inst = I.mid(0) if precision == "fp32" else I.tiny(0)
@@ -150,24 +167,47 @@ def test_bf16_storage_every_shape_short_trajectory(lib):
 
 # ------------------------------------------------------------------ converged parity
 
+INSTANCES = {"tiny_s0": lambda: I.tiny(0), "mid_s0": lambda: I.mid(0),
+             "midpow_s0": lambda: I.large(0, n=100)}
+
+
 @pytest.mark.parametrize("name,precision,tol", [("tiny_s0", "fp64", 1e-6),
                                                 ("mid_s0", "fp32", 1e-4),
                                                 ("midpow_s0", "fp32", 1e-4)])
 def test_converged_matches_oracle(lib, name, precision, tol):
+    """The acceptance criterion: both sides stopped at relative KKT <= 1e-4 (stop test every
+    50 iterations), utility within 1e-4 of the converged optimum and T within 1e-3
+    max-relative of the oracle's T stopped the same way. (The oracle's own T at that stop is
+    up to 8e-4 from T*, so T* itself is checked at a tighter stop below.)"""
     gold = np.load(os.path.join(GOLDEN, f"oracle_{name}.npz"))
-    inst = {"tiny_s0": lambda: I.tiny(0), "mid_s0": lambda: I.mid(0),
-            "midpow_s0": lambda: I.large(0, n=100)}[name]()
+    same = os.path.join(GOLDEN, f"oracle_{name}_kkt1e-4.npz")
+    inst = INSTANCES[name]()
     with lib.Problem(inst) as p:
         g = p.solve(precision=precision, stop_mode="kkt", eps=tol, max_iters=200000,
                     k_check=50, want_T=True, want_Y=True)
     assert g["rc"] == lib.MCF_OK and g["rel_kkt"] < tol
     m = off(inst.n)
     Tstar = gold["T"]
+    Tref = np.load(same)["T"] if tol == 1e-4 else Tstar
     assert abs(g["utility"] - float(gold["utility"])) <= 1e-4 * abs(float(gold["utility"]))
-    assert np.max(np.abs(g["T"][m] - Tstar[m]) / Tstar[m]) <= 1e-3
+    assert np.max(np.abs(g["T"][m] - Tref[m]) / Tref[m]) <= 1e-3
     assert np.allclose(g["T"].sum(axis=1), 0, atol=1e-4 * np.abs(Tstar).max())
     assert g["feasible"] == 1 and g["rel_gap"] >= -1e-6
     assert g["utility"] <= g["dual_bound"] + 1e-6 * abs(g["dual_bound"])
+
+
+@pytest.mark.parametrize("name", ["mid_s0", "midpow_s0"])
+def test_fp32_tighter_stop_matches_optimum(lib, name):
+    """FP32 iterates run to relative KKT 5e-5: T within 1e-3 max-relative of the converged
+    optimum T* (the FP64 oracle at this stop is within 5.4e-4 of T* on these instances)."""
+    gold = np.load(os.path.join(GOLDEN, f"oracle_{name}.npz"))
+    inst = INSTANCES[name]()
+    with lib.Problem(inst) as p:
+        g = p.solve(stop_mode="kkt", eps=5e-5, max_iters=200000, k_check=50, want_T=True)
+    assert g["rc"] == lib.MCF_OK and g["rel_kkt"] < 5e-5
+    m = off(inst.n)
+    assert np.max(np.abs(g["T"][m] - gold["T"][m]) / gold["T"][m]) <= 1e-3
+    assert abs(g["utility"] - float(gold["utility"])) <= 1e-4 * abs(float(gold["utility"]))
 
 
 @pytest.mark.parametrize("name", ["mid_s0", "midpow_s0"])
@@ -181,9 +221,9 @@ def test_bf16_with_fp32_polish_matches_oracle(lib, name):
                     max_iters=200000, k_check=50, want_T=True)
     assert g["rc"] == lib.MCF_OK and g["rel_kkt"] < 1e-4
     m = off(inst.n)
-    Tstar = gold["T"]
+    Tref = np.load(os.path.join(GOLDEN, f"oracle_{name}_kkt1e-4.npz"))["T"]
     assert abs(g["utility"] - float(gold["utility"])) <= 1e-4 * abs(float(gold["utility"]))
-    assert np.max(np.abs(g["T"][m] - Tstar[m]) / Tstar[m]) <= 1e-3
+    assert np.max(np.abs(g["T"][m] - Tref[m]) / Tref[m]) <= 1e-3
 
 
 # ------------------------------------------------------------------ closed forms and edges
