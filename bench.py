@@ -78,18 +78,20 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def algorithmic_bytes(n: int, m: int, s_f: int, s_p: int = 4) -> dict:
+def algorithmic_bytes(n: int, m: int, s_f: int, s_p: int = 4, kind: int = 0) -> dict:
     """Bytes each kernel must move per launch (each array touched once):
     edge:   read F^{k-1/2}, write F^{k+1/2} (2 s_F n m), read Y once (s_P n^2), 16 m of
-            incidence, capacity and mu;
+            incidence, capacity and mu; kinds 1 and 2 also write the in-sums (s_P n^2);
     node:   read F^{k+1/2} once (s_F n m), read Y, W, P and write Y, P (5 s_P n^2), 4(m+2n);
+            kinds 1 and 2 also read the in-sums (s_P n^2);
     check:  read F^{k-1/2} once (s_F n m), read Y, U', Y^ once (3 s_P n^2), 12 m;
     iteration (edge + node): 3 s_F n m + 6 s_P n^2 + ~20 m; the method's floor of
     2 s_F n m + 3 s_P n^2 is reported beside it."""
     nm, n2 = float(n) * m, float(n) * n
+    pin = s_p * n2 if kind in (1, 2) else 0.0
     return {
-        "edge": 2 * s_f * nm + s_p * n2 + 16 * m,
-        "node": s_f * nm + 5 * s_p * n2 + 4 * (m + 2 * n),
+        "edge": 2 * s_f * nm + s_p * n2 + 16 * m + pin,
+        "node": s_f * nm + 5 * s_p * n2 + 4 * (m + 2 * n) + pin,
         "check": s_f * nm + 3 * s_p * n2 + 12 * m,
         "scalar": 0.0,
         "iteration_floor": 2 * s_f * nm + 3 * s_p * n2,
@@ -232,7 +234,8 @@ def run_ours(args, rank, world, local_rank):
     s_f = {"fp32": 4, "bf16": 2, "fp64": 8}[prec]
     s_p = 8 if prec == "fp64" else 4
     common = dict(precision=prec, device=local_rank, k_check=args.k_check,
-                  cuda_stream=stream.cuda_stream, stop_mode="none", shape=args.shape)
+                  cuda_stream=stream.cuda_stream, stop_mode="none", shape=args.shape,
+                  compensated_duals=args.compensated_duals)
 
     def barrier():
         if world > 1:
@@ -258,7 +261,9 @@ def run_ours(args, rank, world, local_rank):
     launches = sum(v[1] for k, v in times.items() if k != "ms_total")
 
     # ---- roofline of the dominant kernel
-    alg = algorithmic_bytes(n, m, s_f, s_p)
+    used_shape = res.get("shape", -1)
+    kind = B.mcf_shape_info()[used_shape][3] if used_shape >= 0 else 0
+    alg = algorithmic_bytes(n, m, s_f, s_p, kind)
     dom = max(("edge", "node", "check"), key=lambda k: times[k][0])
     dom_ms = times[dom][0] / max(times[dom][1], 1)
     peak, peak_kind = peaks()
@@ -315,7 +320,9 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: {wl['desc']}", "n": n, "m": m,
                    "precision": prec, "storage_F": {"fp32": "f32", "bf16": "bf16", "fp64": "f64"}[prec],
-                   "k_check": args.k_check, "seed": args.seed, "shape": args.shape,
+                   "k_check": args.k_check, "seed": args.seed, "shape": used_shape,
+                   "compensated_duals": args.compensated_duals,
+                   "kernel_kind": ["register", "bulk-copy pipelined", "register with in-sums"][kind],
                    "l2": "inputs larger than L2 (F alone is %.1f GB)" % (2 * s_f * n * m / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
@@ -515,6 +522,8 @@ def main():
     ap.add_argument("--k-check", dest="k_check", type=int, default=50)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--shape", type=int, default=-1, help="kernel shape index (-1 = automatic)")
+    ap.add_argument("--compensated-duals", dest="compensated_duals", type=int, default=1,
+                    help="FP32 head + BF16 tail duals (1, the library default) or plain FP32 (0)")
     ap.add_argument("--ttt", action="store_true", help="also time a solve to --ttt-eps")
     ap.add_argument("--ttt-eps", dest="ttt_eps", type=float, default=1e-4)
     ap.add_argument("--ttt-max-iters", dest="ttt_max_iters", type=int, default=20000)

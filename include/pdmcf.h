@@ -86,9 +86,9 @@ typedef struct mcf_options {
   double  omega0;            /* initial primal weight for cold starts (default 1.0)         */
   int     stall_checks;      /* stop when the relative KKT measure has not improved by 5 %
                                 over this many consecutive checks while within 100x of eps
-                                (FP32 iterates reach a rounding floor); 0 = never. The result
-                                then has stalled = 1 and status MCF_ERR_NOT_CONVERGED.
-                                Default 20                                                  */
+                                (FP32 iterates reach a rounding floor); the count restarts
+                                when omega stops adapting; 0 = never. The result then has
+                                stalled = 1 and status MCF_ERR_NOT_CONVERGED. Default 100   */
   int     compensated_duals; /* FP32/BF16 iterates: keep Y as an FP32 head plus a BF16 tail
                                 so the dual update is not limited by FP32 spacing of large
                                 duals (default 1; ignored for MCF_FP64)                     */
@@ -220,6 +220,7 @@ typedef struct mcf_kernel_times {
   double  ms[4];         /* summed device time per kernel kind                        */
   int64_t launches[4];   /* launches per kernel kind                                  */
   double  ms_total;      /* first to last event of the iteration launches             */
+  int     shape;         /* launch shape the solve used (an mcf_shape_info index)     */
 } mcf_kernel_times;
 
 /* As mcf_solve, but launches every kernel individually (no CUDA graphs) with a CUDA event

@@ -313,9 +313,10 @@ def pdmcf(n, tail, head, cap, kind, w, gamma=None, *, eps=1e-6, stop_mode="kkt",
     Y^0 = I - 1 1^T, omega^0 = 1 (Sec. 2.5) unless a warm start is given.
 
     omega stops adapting from iteration omega_freeze_iter on, and (adapt_guard > 0) from
-    the iteration after a stop test whose rel_kkt exceeds adapt_guard times the smallest
-    rel_kkt of this run: Sec. 2.4 allows ending the adaptation after some iterations, a
-    constant omega keeping the convergence proof; the guard is the point it is applied at.
+    the iteration after a stop test whose finite rel_kkt exceeds adapt_guard times the
+    smallest finite rel_kkt of this run: Sec. 2.4 allows ending the adaptation after some
+    iterations, a constant omega keeping the convergence proof; the guard is the point it is
+    applied at (an infinite measure, T outside the domain, is not compared).
     adapt_guard = 0 is the adaptation without that stop.
     """
     tail = np.asarray(tail, dtype=np.int64)
@@ -368,7 +369,7 @@ def pdmcf(n, tail, head, cap, kind, w, gamma=None, *, eps=1e-6, stop_mode="kkt",
         if (k + 1) % k_check == 0 or k + 1 >= max_iters:
             met = metrics(Fhat, Yhat, Q, A, c, util)
             r = met.r
-            if adapt_guard > 0:
+            if adapt_guard > 0 and math.isfinite(met.rel_kkt):
                 if met.rel_kkt > adapt_guard * best_kkt and \
                         (omega_freeze_iter < 0 or omega_freeze_iter > k + 1):
                     omega_freeze_iter = k + 1

@@ -59,7 +59,8 @@ class mcf_result(C.Structure):
 
 
 class mcf_kernel_times(C.Structure):
-    _fields_ = [("ms", C.c_double * 4), ("launches", C.c_int64 * 4), ("ms_total", C.c_double)]
+    _fields_ = [("ms", C.c_double * 4), ("launches", C.c_int64 * 4), ("ms_total", C.c_double),
+                ("shape", C.c_int)]
 
 
 KERNEL_KINDS = ("edge", "node", "check", "scalar")
@@ -257,6 +258,7 @@ def mcf_solve_timed(h, opts: mcf_options, n, m, want_T=False) -> tuple[dict, dic
     times["ms_total"] = kt.ms_total
     out = _result_dict(res, bufs)
     out["rc"] = rc
+    out["shape"] = kt.shape
     return out, times
 
 

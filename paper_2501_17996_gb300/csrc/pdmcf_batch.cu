@@ -62,6 +62,12 @@ __global__ void __launch_bounds__(256) batch_scalar_kernel(BatchScalarArgs a) {
     const double nm = (double)I.n * (double)I.m;
     if (bs->stop_mode == MCF_STOP_PAPER && s->r < nm * bs->eps) stop = true;
     if (bs->stop_mode == MCF_STOP_REL_KKT && s->rel_kkt < bs->eps) stop = true;
+    const int frozen = (s->freeze >= 0 && s->freeze <= s->k) ? 1 : 0;
+    if (frozen != bs->stall_frozen) {   // constant omega from here on: a new phase
+      bs->stall_frozen = frozen;
+      bs->stall_best = INFINITY;
+      bs->stall_count = 0;
+    }
     if (!stop && bs->stop_mode == MCF_STOP_REL_KKT && bs->stall_checks > 0 &&
         s->rel_kkt < 100.0 * bs->eps) {
       if (s->rel_kkt < 0.95 * bs->stall_best) { bs->stall_best = s->rel_kkt; bs->stall_count = 0; }
@@ -237,6 +243,7 @@ int BatchEngine::add(mcf_problem* p, const mcf_options& o, void* tag, int* slot_
   hs.eps = o.eps;
   hs.stall_checks = o.stall_checks;
   hs.stall_best = INFINITY;
+  hs.stall_frozen = 0;
   BCK(cudaMemcpyAsync(d_insts_ + s, &bi, sizeof(bi), cudaMemcpyHostToDevice, stream_));
   BCK(cudaMemcpyAsync(d_sc_ + s, &hs, sizeof(hs), cudaMemcpyHostToDevice, stream_));
   BCK(cudaStreamSynchronize(stream_));

@@ -29,6 +29,7 @@ struct BatchScalars {
   int stall_count;
   int stalled;
   double stall_best;
+  int stall_frozen;        // omega had stopped adapting when the count last restarted
 };
 
 struct BatchInst {

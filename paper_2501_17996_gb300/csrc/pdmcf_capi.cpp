@@ -158,7 +158,7 @@ void mcf_options_default(mcf_options* o) {
   o->device = 0;
   o->cuda_stream = nullptr;
   o->omega0 = 1.0;       // Sec. 2.5
-  o->stall_checks = 20;
+  o->stall_checks = 100;
   o->compensated_duals = 1;
   o->autotune = 1;
   o->shape = -1;

@@ -444,9 +444,9 @@ static __device__ __forceinline__ void scalar_update(DevScalars* s, double dF2, 
     s->check_k = k + 1;
     if (!isfinite(Psum) && feasible) s->numeric_error = 1;
     // Sec. 2.4: omega may stop adapting after some iterations (a constant omega keeps the
-    // convergence proof); it stops from the next iteration once the measure has risen
-    // above guard x its smallest value in this solve
-    if (s->guard > 0.0) {
+    // convergence proof); it stops from the next iteration once the finite measure has
+    // risen above guard x its smallest finite value in this solve
+    if (s->guard > 0.0 && isfinite(s->rel_kkt)) {
       if (s->rel_kkt > s->guard * s->best_kkt && (s->freeze < 0 || s->freeze > k + 1))
         s->freeze = k + 1;
       if (s->rel_kkt < s->best_kkt) s->best_kkt = s->rel_kkt;

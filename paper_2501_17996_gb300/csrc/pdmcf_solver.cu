@@ -693,7 +693,10 @@ static int solve_t(mcf_problem* p, DeviceState* d, const mcf_options* o, mcf_res
   const int kc = std::max(1, o->k_check);
   bool use_graphs = o->use_graphs && !d->graphs_broken && kt == nullptr;
   EventPool pool;
-  if (kt) std::memset(kt, 0, sizeof(*kt));
+  if (kt) {
+    std::memset(kt, 0, sizeof(*kt));
+    kt->shape = d->tma < 0 ? d->shape : NUM_SHAPES + (d->tma_kind == 2 ? NUM_TMA : 0) + d->tma;
+  }
   if (use_graphs && (d->graph_len != kc || d->graph_rho != o->rho || d->graph_stream != st ||
                      d->graph_lo != lo)) {
     destroy_graphs(d);
@@ -708,6 +711,7 @@ static int solve_t(mcf_problem* p, DeviceState* d, const mcf_options* o, mcf_res
   int since_best = 0;
   double floor_best = INFINITY;
   int floor_since = 0;
+  bool floor_frozen = false;   // omega had stopped adapting when the count last restarted
   bool stalled = false;
   int status = MCF_ERR_NOT_CONVERGED;
   if (o->stop_mode == MCF_STOP_NONE) status = MCF_OK;
@@ -751,6 +755,8 @@ static int solve_t(mcf_problem* p, DeviceState* d, const mcf_options* o, mcf_res
     if (o->stop_mode == MCF_STOP_REL_KKT && h.rel_kkt < o->eps) { status = MCF_OK; break; }
     if (rule.handoff > 0.0 && h.rel_kkt < rule.handoff) break;
     if (o->stop_mode == MCF_STOP_REL_KKT && o->stall_checks > 0 && h.rel_kkt < 100.0 * o->eps) {
+      const bool frozen = h.freeze >= 0 && h.freeze <= h.k;
+      if (frozen != floor_frozen) { floor_frozen = frozen; floor_best = INFINITY; floor_since = 0; }
       if (h.rel_kkt < 0.95 * floor_best) { floor_best = h.rel_kkt; floor_since = 0; }
       else if (++floor_since >= o->stall_checks) { stalled = true; break; }
     }

@@ -49,7 +49,7 @@ def test_batch_trajectories_match_oracle(lib):
     _, res = lib.mcf_solve_batch(probs, opts, want_T=True, want_Y=True)
     for inst, r in zip(insts, res):
         ref = O.pdmcf(inst.n, inst.tail, inst.head, inst.cap, inst.kind, inst.w, inst.gamma,
-                      stop_mode="none", max_iters=K)
+                      stop_mode="none", max_iters=K, k_check=10)
         m = off(inst.n)
         assert r["iters"] == K
         scale = np.abs(ref.T[m]).max()

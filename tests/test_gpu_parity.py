@@ -27,9 +27,11 @@ def off(n):
     return ~np.eye(n, dtype=bool)
 
 
-def oracle_k(inst, K):
+def oracle_k(inst, K, k_check):
+    """K oracle iterations with the stop tests (and so the adaptation stop) every k_check
+    iterations, as in the GPU solve it is compared with."""
     return O.pdmcf(inst.n, inst.tail, inst.head, inst.cap, inst.kind, inst.w, inst.gamma,
-                   stop_mode="none", max_iters=K)
+                   stop_mode="none", max_iters=K, k_check=k_check)
 
 
 def rel_err(a, b, mask=None):
@@ -71,7 +73,7 @@ def _pair_gamma():
 def test_fp64_trajectory_matches_oracle(lib, case):
     inst = TRAJ_CASES[case]()
     K = 200
-    ref = oracle_k(inst, K)
+    ref = oracle_k(inst, K, 25)
     with lib.Problem(inst) as p:
         g = p.solve(precision="fp64", stop_mode="none", max_iters=K, k_check=25,
                     want_T=True, want_F=True, want_Y=True)
@@ -105,7 +107,7 @@ def test_adaptation_stop_matches_oracle(lib):
 def test_every_shape_matches_oracle(lib, precision):
     inst = I.mid(0) if precision == "fp32" else I.tiny(0)
     K = 30
-    ref = oracle_k(inst, K)
+    ref = oracle_k(inst, K, 10)
     m = off(inst.n)
     tol = 1e-4 if precision == "fp32" else 1e-9
     shapes = shapes_for(lib, inst, precision)
@@ -123,7 +125,7 @@ def test_slice_trajectory_fp32(lib):
     """The large recipe (power utility, gamma = 1/2, lognormal capacities) at n = 1000."""
     inst = I.large_slice(0)
     K = 12
-    ref = oracle_k(inst, K)
+    ref = oracle_k(inst, K, 4)
     with lib.Problem(inst) as p:
         g = p.solve(precision="fp32", stop_mode="none", max_iters=K, k_check=4,
                     want_T=True, want_Y=True)
@@ -137,7 +139,7 @@ def test_slice_pipelined_shapes_fp32(lib):
     groups of several edges, head-aligned CTA ranges, in-sums consumed by the node phase."""
     inst = I.large_slice(1)
     K = 6
-    ref = oracle_k(inst, K)
+    ref = oracle_k(inst, K, 3)
     m = off(inst.n)
     piped = [s for s, (g, v, b, t) in enumerate(lib.mcf_shape_info()) if t]
     assert piped
@@ -154,7 +156,7 @@ def test_bf16_storage_every_shape_short_trajectory(lib):
     is rounded, so the bound is 1e-2 of scale; indexing mistakes give O(1) errors."""
     inst = I.mid(0)
     K = 3
-    ref = oracle_k(inst, K)
+    ref = oracle_k(inst, K, K)
     m = off(inst.n)
     shapes = shapes_for(lib, inst, "bf16")
     with lib.Problem(inst) as p:
@@ -373,5 +375,5 @@ def test_autotune_picks_a_working_shape(lib):
         shapes = lib.mcf_shape_info()
         assert 0 <= shape < len(shapes) and ms > 0
         g = p.solve(stop_mode="none", max_iters=30, k_check=10, shape=shape, want_T=True)
-    ref = oracle_k(inst, 30)
+    ref = oracle_k(inst, 30, 10)
     assert rel_err(g["T"], ref.T, off(inst.n)) < 1e-4
