@@ -99,9 +99,11 @@ typedef struct mcf_options {
                                 mcf_shape_info. Lets tests and the tuner pick any shape
                                 whose capacity covers the problem                          */
   double  adapt_guard;       /* stop adapting omega (keep it constant, Sec. 2.4) from the
-                                iteration after a stop test whose relative KKT measure
-                                exceeds adapt_guard x the smallest one of this solve;
+                                iteration after a stop test whose finite relative KKT
+                                measure exceeds adapt_guard x the smallest one of this
+                                solve, once that smallest one is below adapt_guard_below;
                                 0 = adapt throughout (default 10)                          */
+  double  adapt_guard_below; /* see adapt_guard (default 1e-2)                             */
 } mcf_options;
 
 /* ---------------------------------------------------------------- results */

@@ -305,7 +305,7 @@ class Result:
 def pdmcf(n, tail, head, cap, kind, w, gamma=None, *, eps=1e-6, stop_mode="kkt",
           max_iters=100000, rho=1.9, theta=0.5, k_adapt=100, tau=1e-5,
           omega_freeze_iter=-1, k_check=1, F0=None, Y0=None, omega0=1.0,
-          adapt_guard=10.0, history=False) -> Result:
+          adapt_guard=10.0, adapt_guard_below=1e-2, history=False) -> Result:
     """Algorithm 2.1 (PDMCF), float64.
 
     stop_mode: "paper" stops when r^k < n m eps (Sec. 2.5), "kkt" when rel_kkt^k < eps,
@@ -314,9 +314,10 @@ def pdmcf(n, tail, head, cap, kind, w, gamma=None, *, eps=1e-6, stop_mode="kkt",
 
     omega stops adapting from iteration omega_freeze_iter on, and (adapt_guard > 0) from
     the iteration after a stop test whose finite rel_kkt exceeds adapt_guard times the
-    smallest finite rel_kkt of this run: Sec. 2.4 allows ending the adaptation after some
-    iterations, a constant omega keeping the convergence proof; the guard is the point it is
-    applied at (an infinite measure, T outside the domain, is not compared).
+    smallest finite rel_kkt of this run, once that smallest value is below
+    adapt_guard_below (the final phase; earlier swings of the measure are the normal
+    transient). Sec. 2.4 allows ending the adaptation after some iterations, a constant
+    omega keeping the convergence proof; the guard is the point it is applied at.
     adapt_guard = 0 is the adaptation without that stop.
     """
     tail = np.asarray(tail, dtype=np.int64)
@@ -370,7 +371,7 @@ def pdmcf(n, tail, head, cap, kind, w, gamma=None, *, eps=1e-6, stop_mode="kkt",
             met = metrics(Fhat, Yhat, Q, A, c, util)
             r = met.r
             if adapt_guard > 0 and math.isfinite(met.rel_kkt):
-                if met.rel_kkt > adapt_guard * best_kkt and \
+                if best_kkt < adapt_guard_below and met.rel_kkt > adapt_guard * best_kkt and \
                         (omega_freeze_iter < 0 or omega_freeze_iter > k + 1):
                     omega_freeze_iter = k + 1
                 best_kkt = min(best_kkt, met.rel_kkt)

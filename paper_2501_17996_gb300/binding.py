@@ -43,6 +43,7 @@ class mcf_options(C.Structure):
         ("use_graphs", C.c_int), ("device", C.c_int), ("cuda_stream", C.c_void_p),
         ("omega0", C.c_double), ("stall_checks", C.c_int), ("compensated_duals", C.c_int),
         ("autotune", C.c_int), ("shape", C.c_int), ("adapt_guard", C.c_double),
+        ("adapt_guard_below", C.c_double),
     ]
 
 

@@ -229,6 +229,7 @@ int BatchEngine::add(mcf_problem* p, const mcf_options& o, void* tag, int* slot_
   d.k_adapt = o.k_adapt > 0 ? o.k_adapt : 1;
   d.freeze = o.omega_freeze_iter;
   d.guard = o.adapt_guard;
+  d.guard_below = o.adapt_guard_below;
   d.best_kkt = INFINITY;
   d.r = INFINITY;
   d.rel_kkt = INFINITY;

@@ -126,6 +126,8 @@ int validate_options(const mcf_options* o) {
   if (o->shape < -1 || o->shape >= mcf_shape_count()) return fail(MCF_ERR_INVALID, "unknown shape");
   if (!(o->adapt_guard >= 0.0) || !std::isfinite(o->adapt_guard))
     return fail(MCF_ERR_INVALID, "adapt_guard must be finite and >= 0");
+  if (!(o->adapt_guard_below > 0.0))
+    return fail(MCF_ERR_INVALID, "adapt_guard_below must be > 0");
   return MCF_OK;
 }
 
@@ -163,6 +165,7 @@ void mcf_options_default(mcf_options* o) {
   o->autotune = 1;
   o->shape = -1;
   o->adapt_guard = 10.0;
+  o->adapt_guard_below = 1e-2;
 }
 
 int mcf_create_problem(int32_t n, int32_t m, const int32_t* tail, const int32_t* head,

@@ -268,6 +268,8 @@ __device__ __forceinline__ P prox_log(P y, P beta, P w) {
 // c2 = beta (1/gamma - 1)(w gamma)^(1/(1-gamma)). h is increasing and convex on
 // [max(0,-y), inf); Newton from t_hi = max(0,-y) + (c1 c2)^(1/(c1+2)) (where h >= 0)
 // decreases monotonically to the root. gamma = 1/2 (c1 = 1) avoids transcendental calls.
+// (Starting from the previous dual instead saves iterations on average but not per warp,
+// whose slowest lane sets the time; measured slower.)
 template <typename P>
 __device__ __forceinline__ P prox_pow(P y, P beta, P w, P gamma) {
   const P tlo = y < P(0) ? -y : P(0);
@@ -444,10 +446,11 @@ static __device__ __forceinline__ void scalar_update(DevScalars* s, double dF2, 
     s->check_k = k + 1;
     if (!isfinite(Psum) && feasible) s->numeric_error = 1;
     // Sec. 2.4: omega may stop adapting after some iterations (a constant omega keeps the
-    // convergence proof); it stops from the next iteration once the finite measure has
-    // risen above guard x its smallest finite value in this solve
+    // convergence proof); it stops from the next iteration once, in the final phase (best
+    // finite measure below guard_below), the measure has risen above guard x that best
     if (s->guard > 0.0 && isfinite(s->rel_kkt)) {
-      if (s->rel_kkt > s->guard * s->best_kkt && (s->freeze < 0 || s->freeze > k + 1))
+      if (s->best_kkt < s->guard_below && s->rel_kkt > s->guard * s->best_kkt &&
+          (s->freeze < 0 || s->freeze > k + 1))
         s->freeze = k + 1;
       if (s->rel_kkt < s->best_kkt) s->best_kkt = s->rel_kkt;
     }
@@ -600,7 +603,7 @@ edge_kernel(IterArgs<P, S> a) {
   S* __restrict__ Fn = a.F[a.parity ^ 1];
   const P* __restrict__ Y = a.Y[a.parity];
   const __nv_bfloat16* __restrict__ ylo = a.Ylo[a.parity];
-  double dsum = 0.0;
+  P dsum = P(0);   // this thread's ||dF||^2 over its edges (FP64 across threads)
 
   int nh = 0, nt = 0;
   P nc = P(0), nmu = P(0), nmul = P(0);
@@ -673,7 +676,7 @@ edge_kernel(IterArgs<P, S> a) {
         st_stream<S, VW>(Fn + (size_t)e * a.ld + ci * VW, out);
       }
     }
-    dsum += (double)dloc;
+    dsum += dloc;
     if (lane == 0) {
       P hi, lo;
       shifted_mu<P>(mu0, mu0l, mu, hi, lo);
@@ -681,7 +684,7 @@ edge_kernel(IterArgs<P, S> a) {
       a.mu_lo[e] = lo;
     }
   }
-  double v1[1] = {dsum};
+  double v1[1] = {(double)dsum};
   block_sum_write<BLOCK, 1>(v1, a.part_edge + blockIdx.x);
 }
 
@@ -899,7 +902,7 @@ edge_tma_kernel(IterArgs<float, S> a) {
     if (cnt > 0) issue(0);
     if (cnt > 1) issue(1);
   }
-  double dsum = 0.0;
+  P dsum = P(0);   // this thread's ||dF||^2 over its edges (FP64 across threads)
   int cur_h = -1;
   const __nv_bfloat16* __restrict__ ylo = a.Ylo[a.parity];
   P yh[VPT][VW], yhl[VPT][VW], sin_[VPT][VW];   // head's Y (hi, tail) and the in-sum
@@ -1005,7 +1008,7 @@ edge_tma_kernel(IterArgs<float, S> a) {
         st_stream<S, VW>(Fn + (size_t)e * a.ld + ci * VW, out);
       }
     }
-    dsum += (double)dloc;
+    dsum += dloc;
     if (tid == 0) {
       P hi, lo;
       shifted_mu<P>(mu_e, mu_el, mu, hi, lo);
@@ -1021,7 +1024,7 @@ edge_tma_kernel(IterArgs<float, S> a) {
       if (ci < nchunks) st_plain<P, VW>(pr + ci * VW, sin_[v]);
     }
   }
-  double v1[1] = {dsum};
+  double v1[1] = {(double)dsum};
   block_sum_write<BLOCK, 1>(v1, a.part_edge + blockIdx.x);
 }
 
@@ -1050,7 +1053,7 @@ edge_insum_kernel(IterArgs<P, S> a) {
   const P* __restrict__ Y = a.Y[a.parity];
   const __nv_bfloat16* __restrict__ ylo = a.Ylo[a.parity];
   const int e0 = a.cta_ptr[blockIdx.x], e1 = a.cta_ptr[blockIdx.x + 1];
-  double dsum = 0.0;
+  P dsum = P(0);   // this thread's ||dF||^2 over its edges (FP64 across threads)
   int cur_h = -1;
   auto flush = [&](int hh) {
     P* pr = a.Pin + (size_t)hh * a.ld;
@@ -1149,7 +1152,7 @@ edge_insum_kernel(IterArgs<P, S> a) {
         st_plain<P, VW>(sin_s + ci * VW, acc);
       }
     }
-    dsum += (double)dloc;
+    dsum += dloc;
     if (tid == 0) {
       P hi, lo;
       shifted_mu<P>(mu0, mu0l, mu, hi, lo);
@@ -1158,7 +1161,7 @@ edge_insum_kernel(IterArgs<P, S> a) {
     }
   }
   if (cur_h >= 0) flush(cur_h);
-  double v1[1] = {dsum};
+  double v1[1] = {(double)dsum};
   block_sum_write<BLOCK, 1>(v1, a.part_edge + blockIdx.x);
 }
 

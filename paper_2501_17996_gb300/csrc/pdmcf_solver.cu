@@ -675,6 +675,7 @@ static int solve_t(mcf_problem* p, DeviceState* d, const mcf_options* o, mcf_res
   h.k_adapt = o->k_adapt > 0 ? o->k_adapt : 1;
   h.freeze = o->omega_freeze_iter;
   h.guard = o->adapt_guard;
+  h.guard_below = o->adapt_guard_below;
   h.best_kkt = INFINITY;
   h.r = INFINITY;
   h.rel_kkt = INFINITY;
