@@ -174,7 +174,7 @@ def oracle_iters_per_s(sample, k_check: int, steps: int, warmup: int):
     return steps / dt, dt
 
 
-def cpu_baseline(wl, inst, seed, k_check, steps=6, warmup=1):
+def cpu_baseline(wl, inst, seed, k_check, steps=20, warmup=1):
     sample = wl["sample"](seed)
     ips, dt = oracle_iters_per_s(sample, k_check, steps, warmup)
     scale = (sample.n * sample.m) / float(inst.n * inst.m)

@@ -312,13 +312,15 @@ def pdmcf(n, tail, head, cap, kind, w, gamma=None, *, eps=1e-6, stop_mode="kkt",
     "none" runs exactly max_iters iterations. Initialisation F^{-1/2} = 0,
     Y^0 = I - 1 1^T, omega^0 = 1 (Sec. 2.5) unless a warm start is given.
 
-    omega stops adapting from iteration omega_freeze_iter on, and (adapt_guard > 0) from
-    the iteration after a stop test whose finite rel_kkt exceeds adapt_guard times the
-    smallest finite rel_kkt of this run, once that smallest value is below
-    adapt_guard_below (the final phase; earlier swings of the measure are the normal
-    transient). Sec. 2.4 allows ending the adaptation after some iterations, a constant
-    omega keeping the convergence proof; the guard is the point it is applied at.
-    adapt_guard = 0 is the adaptation without that stop.
+    omega stops adapting from iteration omega_freeze_iter on, and (adapt_guard > 0) in the
+    final phase: it begins at the first stop test with a finite rel_kkt below
+    adapt_guard_below (omega_arm = omega then); in it omega stops adapting from the
+    iteration after a stop test whose finite rel_kkt exceeds adapt_guard times the smallest
+    one so far, or where omega has moved more than a factor adapt_guard away from
+    omega_arm. Sec. 2.4 allows ending the adaptation after some iterations, a constant omega
+    keeping the convergence proof; the guard is the point it is applied at (the rule of
+    Eq. e-primal_weight can run away: omega -> 0 or infinity). adapt_guard = 0 is the
+    adaptation without that stop.
     """
     tail = np.asarray(tail, dtype=np.int64)
     head = np.asarray(head, dtype=np.int64)
@@ -337,6 +339,7 @@ def pdmcf(n, tail, head, cap, kind, w, gamma=None, *, eps=1e-6, stop_mode="kkt",
     Fhat = Yhat = mu = None
     hist = []
     best_kkt = math.inf
+    omega_arm = 0.0
     status = "max_iters"
     k = 0
     while True:
@@ -371,10 +374,13 @@ def pdmcf(n, tail, head, cap, kind, w, gamma=None, *, eps=1e-6, stop_mode="kkt",
             met = metrics(Fhat, Yhat, Q, A, c, util)
             r = met.r
             if adapt_guard > 0 and math.isfinite(met.rel_kkt):
-                if best_kkt < adapt_guard_below and met.rel_kkt > adapt_guard * best_kkt and \
-                        (omega_freeze_iter < 0 or omega_freeze_iter > k + 1):
+                if omega_arm > 0 and (omega_freeze_iter < 0 or omega_freeze_iter > k + 1) and \
+                        (met.rel_kkt > adapt_guard * best_kkt or omega > adapt_guard * omega_arm
+                         or omega * adapt_guard < omega_arm):
                     omega_freeze_iter = k + 1
                 best_kkt = min(best_kkt, met.rel_kkt)
+                if omega_arm == 0 and best_kkt < adapt_guard_below:
+                    omega_arm = omega
             if history:
                 hist.append(dict(k=k + 1, omega=omega, r=r, rel_kkt=met.rel_kkt,
                                  rel_gap=met.rel_gap, rel_cons=met.rel_cons,

@@ -445,21 +445,25 @@ static __device__ __forceinline__ void scalar_update(DevScalars* s, double dF2, 
     s->nonpos_frac = nonpos / ((double)s->n * (double)(s->n - 1));
     s->check_k = k + 1;
     if (!isfinite(Psum) && feasible) s->numeric_error = 1;
-    // Sec. 2.4: omega may stop adapting after some iterations (a constant omega keeps the
-    // convergence proof); it stops from the next iteration once, in the final phase (best
-    // finite measure below guard_below), the measure has risen above guard x that best
-    if (s->guard > 0.0 && isfinite(s->rel_kkt)) {
-      if (s->best_kkt < s->guard_below && s->rel_kkt > s->guard * s->best_kkt &&
-          (s->freeze < 0 || s->freeze > k + 1))
-        s->freeze = k + 1;
-      if (s->rel_kkt < s->best_kkt) s->best_kkt = s->rel_kkt;
-    }
   }
   // Algorithm 2.1, step 3 (Eq. e-primal_weight)
   s->alpha_last = s->alpha;
   s->beta_last = s->beta;
   if (k % s->k_adapt == 0 && dF > s->tau && dY > s->tau && (s->freeze < 0 || k < s->freeze)) {
     s->omega = pow(dY / dF, s->theta) * pow(s->omega, 1.0 - s->theta);
+  }
+  // Sec. 2.4: omega may stop adapting after some iterations (a constant omega keeps the
+  // convergence proof). The final phase begins at the first check with a finite measure
+  // below guard_below (omega_arm records omega then); in it, omega stops adapting from the
+  // next iteration once the measure exceeds guard x its best or omega has moved more than
+  // a factor guard away from omega_arm.
+  if (check && s->guard > 0.0 && isfinite(s->rel_kkt)) {
+    if (s->omega_arm > 0.0 && (s->freeze < 0 || s->freeze > k + 1) &&
+        (s->rel_kkt > s->guard * s->best_kkt || s->omega > s->guard * s->omega_arm ||
+         s->omega * s->guard < s->omega_arm))
+      s->freeze = k + 1;
+    if (s->rel_kkt < s->best_kkt) s->best_kkt = s->rel_kkt;
+    if (s->omega_arm == 0.0 && s->best_kkt < s->guard_below) s->omega_arm = s->omega;
   }
   s->alpha = s->eta / s->omega;
   s->beta = s->eta * s->omega;
@@ -690,7 +694,10 @@ edge_kernel(IterArgs<P, S> a) {
 
 // ------------------------------------------------------------------ node phase
 
-template <typename P, typename S, int VPT, int GROUP, int BLOCK, int MINB, bool PIN = false>
+// CHECK: the variant for check iterations, which also evaluates U(T^), (-u)^*(Y^), the
+// consistency and domain counts and writes T^, U'(T^) and Y^ (the other variant keeps only
+// what every iteration needs, and fewer registers).
+template <typename P, typename S, int VPT, int GROUP, int BLOCK, int MINB, bool PIN, bool CHECK>
 __global__ void __launch_bounds__(BLOCK, MINB)
 node_kernel(IterArgs<P, S> a) {
   constexpr int VW = StoreTraits<S>::VW;
@@ -712,60 +719,16 @@ node_kernel(IterArgs<P, S> a) {
   for (int k = 0; k < NODE_PARTS; ++k) acc[k] = 0.0;
 
   for (int j = gid; j < a.n; j += ngroups) {
-    P s[VPT][VW];
-#pragma unroll
-    for (int v = 0; v < VPT; ++v)
-#pragma unroll
-      for (int u = 0; u < VW; ++u) s[v][u] = P(0);
-    // p_j = sum_{in(j)} f_new - sum_{out(j)} f_new, two edge rows in flight per step. With
-    // PIN the edge phase already summed the in-edges into Pin[j].
+    // p_j = sum_{in(j)} f_new - sum_{out(j)} f_new. With PIN the edge phase already summed
+    // the in-edges into Pin[j]. One 16-byte chunk at a time: its sum over the node's rows
+    // (four rows in flight, added as consecutive pairs), then the dual update of that chunk,
+    // so only one chunk's accumulator is live.
     const int ib = a.in_ptr[j], nin = PIN ? 0 : a.in_ptr[j + 1] - ib;
     const int ob = a.out_ptr[j], deg = nin + (a.out_ptr[j + 1] - ob);
-    if constexpr (PIN) {   // only heads of some edge were written; others sum to zero
-      const P* pr = a.Pin + (size_t)j * a.ld;
-      if (a.in_ptr[j + 1] > ib) {
-#pragma unroll
-        for (int v = 0; v < VPT; ++v) {
-          const int ci = v * GROUP + lane;
-          if (ci < nchunks) ld_plain<P, VW>(pr + ci * VW, s[v]);
-        }
-      }
-    }
+    const bool pin_rows = PIN && a.in_ptr[j + 1] > ib;   // only heads of some edge were written
     auto row = [&](int k) -> const S* {
       return Fn + (size_t)(k < nin ? ib + k : a.out_idx[ob + k - nin]) * a.ld;
     };
-    int k = 0;
-    for (; k + 1 < deg; k += 2) {
-      const S* r0 = row(k);
-      const S* r1 = row(k + 1);
-      const P s0 = k < nin ? P(1) : P(-1);
-      const P s1 = k + 1 < nin ? P(1) : P(-1);
-#pragma unroll
-      for (int v = 0; v < VPT; ++v) {
-        const int ci = v * GROUP + lane;
-        if (ci < nchunks) {
-          S f0[VW], f1[VW];
-          ld_plain<S, VW>(r0 + ci * VW, f0);
-          ld_plain<S, VW>(r1 + ci * VW, f1);
-#pragma unroll
-          for (int u = 0; u < VW; ++u) s[v][u] += s0 * to_p<P>(f0[u]) + s1 * to_p<P>(f1[u]);
-        }
-      }
-    }
-    if (k < deg) {
-      const S* r0 = row(k);
-      const P s0 = k < nin ? P(1) : P(-1);
-#pragma unroll
-      for (int v = 0; v < VPT; ++v) {
-        const int ci = v * GROUP + lane;
-        if (ci < nchunks) {
-          S f0[VW];
-          ld_plain<S, VW>(r0 + ci * VW, f0);
-#pragma unroll
-          for (int u = 0; u < VW; ++u) s[v][u] += s0 * to_p<P>(f0[u]);
-        }
-      }
-    }
     P loc[NODE_PARTS];
 #pragma unroll
     for (int k = 0; k < NODE_PARTS; ++k) loc[k] = P(0);
@@ -773,10 +736,50 @@ node_kernel(IterArgs<P, S> a) {
     const P* yrow = Yo + (size_t)j * a.ld;
     const P* wrow = a.W + (size_t)j * a.ld;
     const P* grow = a.Gm ? a.Gm + (size_t)j * a.ld : nullptr;
-#pragma unroll
+#pragma unroll 1
     for (int v = 0; v < VPT; ++v) {
       const int ci = v * GROUP + lane;
-      if (ci >= nchunks) continue;
+      if (ci >= nchunks) break;
+      P s[VW];
+#pragma unroll
+      for (int u = 0; u < VW; ++u) s[u] = P(0);
+      if (pin_rows) ld_plain<P, VW>(a.Pin + (size_t)j * a.ld + ci * VW, s);
+      int k = 0;
+      for (; k + 3 < deg; k += 4) {
+        const S* r0 = row(k);
+        const S* r1 = row(k + 1);
+        const S* r2 = row(k + 2);
+        const S* r3 = row(k + 3);
+        S f0[VW], f1[VW], f2[VW], f3[VW];
+        ld_plain<S, VW>(r0 + ci * VW, f0);
+        ld_plain<S, VW>(r1 + ci * VW, f1);
+        ld_plain<S, VW>(r2 + ci * VW, f2);
+        ld_plain<S, VW>(r3 + ci * VW, f3);
+        const P s0 = k < nin ? P(1) : P(-1), s1 = k + 1 < nin ? P(1) : P(-1);
+        const P s2 = k + 2 < nin ? P(1) : P(-1), s3 = k + 3 < nin ? P(1) : P(-1);
+#pragma unroll
+        for (int u = 0; u < VW; ++u) s[u] += s0 * to_p<P>(f0[u]) + s1 * to_p<P>(f1[u]);
+#pragma unroll
+        for (int u = 0; u < VW; ++u) s[u] += s2 * to_p<P>(f2[u]) + s3 * to_p<P>(f3[u]);
+      }
+      if (k + 1 < deg) {
+        const S* r0 = row(k);
+        const S* r1 = row(k + 1);
+        S f0[VW], f1[VW];
+        ld_plain<S, VW>(r0 + ci * VW, f0);
+        ld_plain<S, VW>(r1 + ci * VW, f1);
+        const P s0 = k < nin ? P(1) : P(-1), s1 = k + 1 < nin ? P(1) : P(-1);
+#pragma unroll
+        for (int u = 0; u < VW; ++u) s[u] += s0 * to_p<P>(f0[u]) + s1 * to_p<P>(f1[u]);
+        k += 2;
+      }
+      if (k < deg) {
+        S f0[VW];
+        ld_plain<S, VW>(row(k) + ci * VW, f0);
+        const P s0 = k < nin ? P(1) : P(-1);
+#pragma unroll
+        for (int u = 0; u < VW; ++u) s[u] += s0 * to_p<P>(f0[u]);
+      }
       P po[VW], yo[VW], wv[VW], gv[VW], yn[VW];
       ld_plain<P, VW>(prow + ci * VW, po);
       ld_plain<P, VW>(yrow + ci * VW, yo);
@@ -796,7 +799,7 @@ node_kernel(IterArgs<P, S> a) {
 #pragma unroll
       for (int u = 0; u < VW; ++u) {
         const int i = ci * VW + u;
-        const P fhat_at = (s[v][u] - (P(1) - rho) * po[u]) * inv_rho;   // (F^ A^T)_{ij}
+        const P fhat_at = (s[u] - (P(1) - rho) * po[u]) * inv_rho;   // (F^ A^T)_{ij}
         const P fplus_at = P(2) * fhat_at - po[u];                       // (F^{k+1} A^T)_{ij}
         const bool live = (i < a.n) && (i != j);
         // Y^ - Y = -beta (F^{k+1}A^T + t), t = T(Y^) (Moreau): the increment is formed from
@@ -820,7 +823,7 @@ node_kernel(IterArgs<P, S> a) {
         that_v[u] = i < a.n ? th : P(0);
         yh_v[u] = yhat;
         up_v[u] = P(0);
-        if (a.check && live) {
+        if (CHECK && live) {
           if (!(th > P(0))) loc[1] += P(1);
           else {
             loc[2] += util_value<P>(a.kind, th, wv[u], gv[u]);
@@ -840,8 +843,8 @@ node_kernel(IterArgs<P, S> a) {
         if (a.Ylo[a.parity ^ 1]) st_lo<VW>(a.Ylo[a.parity ^ 1] + (size_t)j * a.ld + ci * VW, yl);
       }
       st_plain<P, VW>(Yn + (size_t)j * a.ld + ci * VW, yn);
-      st_plain<P, VW>(prow + ci * VW, s[v]);
-      if (a.check) {
+      st_plain<P, VW>(prow + ci * VW, s);
+      if constexpr (CHECK) {
         st_plain<P, VW>(a.That + (size_t)j * a.ld + ci * VW, that_v);
         st_plain<P, VW>(a.Uprime + (size_t)j * a.ld + ci * VW, up_v);
         st_plain<P, VW>(a.Yhat + (size_t)j * a.ld + ci * VW, yh_v);

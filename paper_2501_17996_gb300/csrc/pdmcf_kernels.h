@@ -24,6 +24,7 @@ template <typename P, typename S>
 struct KernelTable {
   void (*edge[NUM_SHAPES])(IterArgs<P, S>);
   void (*node[NUM_SHAPES])(IterArgs<P, S>);
+  void (*node_chk[NUM_SHAPES])(IterArgs<P, S>);   // the node phase of check iterations
   void (*check[NUM_SHAPES])(IterArgs<P, S>);
 };
 
@@ -38,6 +39,7 @@ template <typename S>
 struct TmaTable {
   void (*edge[NUM_TMA])(IterArgs<float, S>);
   void (*node[NUM_TMA])(IterArgs<float, S>);
+  void (*node_chk[NUM_TMA])(IterArgs<float, S>);
   void (*insum[NUM_TMA])(IterArgs<float, S>);   // register edge phase with in-sums
 };
 const TmaTable<float>& tma_table_f32();
@@ -67,10 +69,17 @@ constexpr int min_blocks() {
                                            : (512 / BLOCK > 0 ? 512 / BLOCK : 1);
 }
 
-// The node phase keeps an accumulator and two gathered rows per chunk: half the residency
-// once those exceed 48 bytes per chunk slot.
+// The node phase works one chunk at a time, so its registers do not grow with VPT: 1024
+// threads per SM.
 template <typename P, int VPT, int VW, int BLOCK>
 constexpr int min_blocks_node() {
+  return 1024 / BLOCK > 0 ? 1024 / BLOCK : 1;
+}
+
+// The batched node phase keeps every chunk's accumulator live: half the residency once they
+// exceed 48 bytes per thread.
+template <typename P, int VPT, int VW, int BLOCK>
+constexpr int min_blocks_batch_node() {
   return (VPT * VW * (int)sizeof(P) <= 48) ? (1024 / BLOCK > 0 ? 1024 / BLOCK : 1)
                                            : (512 / BLOCK > 0 ? 512 / BLOCK : 1);
 }
@@ -82,7 +91,8 @@ void fill_shape(KernelTable<P, S>& t) {
   constexpr int MB = min_blocks<P, d.vpt, StoreTraits<S>::VW, d.block>();
   t.edge[IDX] = edge_kernel<P, S, d.vpt, d.group, d.block, MB>;
   constexpr int MBN = min_blocks_node<P, d.vpt, StoreTraits<S>::VW, d.block>();
-  t.node[IDX] = node_kernel<P, S, d.vpt, d.group, d.block, MBN>;
+  t.node[IDX] = node_kernel<P, S, d.vpt, d.group, d.block, MBN, false, false>;
+  t.node_chk[IDX] = node_kernel<P, S, d.vpt, d.group, d.block, 1, false, true>;
   t.check[IDX] = check_kernel<P, S, d.vpt, d.group, d.block, MB>;
 }
 
@@ -90,7 +100,8 @@ template <typename S, int IDX>
 void fill_tma(TmaTable<S>& t) {
   constexpr int V = kTmaVpt[IDX];
   t.edge[IDX] = edge_tma_kernel<S, V, TMA_BLOCK>;
-  t.node[IDX] = node_kernel<float, S, V, TMA_NODE_BLOCK, TMA_NODE_BLOCK, 1, true>;
+  t.node[IDX] = node_kernel<float, S, V, TMA_NODE_BLOCK, TMA_NODE_BLOCK, 2, true, false>;
+  t.node_chk[IDX] = node_kernel<float, S, V, TMA_NODE_BLOCK, TMA_NODE_BLOCK, 1, true, true>;
   t.insum[IDX] = edge_insum_kernel<float, S, V, TMA_BLOCK>;
 }
 

@@ -482,21 +482,22 @@ static IterArgs<P, S> make_args(DeviceState* d, const mcf_problem* p, double rho
 
 // Edge and node phase launches of one iteration (register shapes or the pipelined pair).
 template <typename P, typename S>
-static cudaError_t launch_phase(DeviceState* d, void** kargs, int which, cudaStream_t st) {
+static cudaError_t launch_phase(DeviceState* d, void** kargs, int which, bool check, cudaStream_t st) {
   if constexpr (!std::is_same<P, double>::value) {
     if (d->tma >= 0) {
       const TmaTable<S>& T = get_tma_table<S>();
       if (which == 0)
         return cudaLaunchKernel(d->tma_kind == 1 ? (const void*)T.edge[d->tma] : (const void*)T.insum[d->tma],
                                 dim3(d->grid_tma), dim3(TMA_BLOCK), kargs, d->tma_smem, st);
-      return cudaLaunchKernel((const void*)T.node[d->tma], dim3(d->grid_node_pin),
-                              dim3(TMA_NODE_BLOCK), kargs, 0, st);
+      return cudaLaunchKernel(check ? (const void*)T.node_chk[d->tma] : (const void*)T.node[d->tma],
+                              dim3(d->grid_node_pin), dim3(TMA_NODE_BLOCK), kargs, 0, st);
     }
   }
   const KernelTable<P, S>& T = get_table<P, S>();
   if (which == 0)
     return cudaLaunchKernel((const void*)T.edge[d->shape], dim3(d->grid_edge), dim3(d->block), kargs, 0, st);
-  return cudaLaunchKernel((const void*)T.node[d->shape], dim3(d->grid_node), dim3(d->block), kargs, 0, st);
+  return cudaLaunchKernel(check ? (const void*)T.node_chk[d->shape] : (const void*)T.node[d->shape],
+                          dim3(d->grid_node), dim3(d->block), kargs, 0, st);
 }
 
 static int edge_blocks(const DeviceState* d) { return d->tma >= 0 ? d->grid_tma : d->grid_edge; }
@@ -510,9 +511,9 @@ static cudaError_t launch_iteration(DeviceState* d, IterArgs<P, S> a, int parity
   a.check = check ? 1 : 0;
   void* kargs[] = {&a};
   cudaError_t e;
-  e = launch_phase<P, S>(d, kargs, 0, st);
+  e = launch_phase<P, S>(d, kargs, 0, check, st);
   if (e != cudaSuccess) return e;
-  e = launch_phase<P, S>(d, kargs, 1, st);
+  e = launch_phase<P, S>(d, kargs, 1, check, st);
   if (e != cudaSuccess) return e;
   if (check) {
     e = cudaLaunchKernel((const void*)T.check[d->shape], dim3(d->grid_check), dim3(d->block), kargs, 0, st);
@@ -553,10 +554,10 @@ static cudaError_t launch_iteration_timed(DeviceState* d, IterArgs<P, S> a, int 
   void* kargs[] = {&a};
   cudaError_t e;
   if (pool.used == 0) cudaEventRecord(pool.next(-1), st);
-  e = launch_phase<P, S>(d, kargs, 0, st);
+  e = launch_phase<P, S>(d, kargs, 0, check, st);
   if (e != cudaSuccess) return e;
   cudaEventRecord(pool.next(0), st);
-  e = launch_phase<P, S>(d, kargs, 1, st);
+  e = launch_phase<P, S>(d, kargs, 1, check, st);
   if (e != cudaSuccess) return e;
   cudaEventRecord(pool.next(1), st);
   if (check) {
@@ -675,6 +676,7 @@ static int solve_t(mcf_problem* p, DeviceState* d, const mcf_options* o, mcf_res
   h.freeze = o->omega_freeze_iter;
   h.guard = o->adapt_guard;
   h.guard_below = o->adapt_guard_below;
+  h.omega_arm = 0.0;
   h.best_kkt = INFINITY;
   h.r = INFINITY;
   h.rel_kkt = INFINITY;

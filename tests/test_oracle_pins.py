@@ -397,8 +397,9 @@ def test_ring_pin_detects_planted_mistakes(monkeypatch):
 
 def test_adaptation_stop_keeps_omega_constant():
     """Sec. 2.4: omega may stop adapting from some iteration on and stays constant after.
-    With the guard the stop comes after the first stop test whose rel_kkt exceeds
-    guard x the smallest one so far, once that smallest one is below 1e-2; before it the run equals the unguarded one, after it
+    With the guard the stop comes after the first stop test, in the final phase (rel_kkt
+    has been below 1e-2), whose rel_kkt exceeds guard x the smallest one so far or whose
+    omega is more than a factor guard away from its value when that phase began; before it the run equals the unguarded one, after it
     omega never changes while the unguarded run keeps adapting."""
     inst = I.mid(0)
     kw = dict(stop_mode="none", max_iters=1500, k_check=50, history=True)
@@ -406,12 +407,17 @@ def test_adaptation_stop_keeps_omega_constant():
     free = O.pdmcf(*args, adapt_guard=0, **kw)
     held = O.pdmcf(*args, adapt_guard=1.05, **kw)
     assert free.omega_frozen_at == -1
-    # first check whose measure is above 1.05 x the best before it, that best below 1e-2
-    best, trigger = math.inf, None
+    # the final phase begins at the first check with rel_kkt below 1e-2 (omega_arm = omega
+    # there); the stop follows the first later check whose measure is above 1.05 x the best
+    # before it or whose omega is more than a factor 1.05 away from omega_arm
+    best, arm, trigger = math.inf, 0.0, None
     for h in free.history:
-        if trigger is None and best < 1e-2 and h["rel_kkt"] > 1.05 * best:
+        if trigger is None and arm > 0 and (h["rel_kkt"] > 1.05 * best or h["omega"] > 1.05 * arm
+                                            or h["omega"] * 1.05 < arm):
             trigger = h["k"]
         best = min(best, h["rel_kkt"])
+        if arm == 0 and best < 1e-2:
+            arm = h["omega"]
     assert trigger is not None and held.omega_frozen_at == trigger
     for a, b in zip(free.history, held.history):
         if a["k"] <= trigger:
