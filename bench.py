@@ -58,7 +58,22 @@ WORKLOADS = {
     "mid": dict(factory=lambda seed: I.mid(seed), sample=lambda seed: I.mid(seed),
                 desc="n=100, m=1000 (ring + 9 random out-edges per node), c~U[1,10], "
                      "u = w log s, w~U[0.5,1.5]"),
+    # the paper's own family (Sec. 3.1); sizes come from --knn-n / --knn-q (set in main)
+    "knn": dict(factory=None, sample=None, desc=None),
 }
+
+
+def knn_connected(n: int, q: int, seed: int):
+    """The kNN instance of the first seed >= `seed` whose graph is strongly connected."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+
+    for s in range(seed, seed + 100):
+        inst = I.knn(n, q, s)
+        g = sp.coo_matrix((np.ones(inst.m), (inst.tail, inst.head)), shape=(n, n))
+        if connected_components(g, directed=True, connection="strong")[0] == 1:
+            return inst
+    raise RuntimeError(f"no strongly connected kNN graph for n={n}, q={q}")
 
 
 def peaks():
@@ -195,7 +210,11 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     wl = WORKLOADS[args.workload]
-    inst_n, inst_m = {"large": (10000, 100000), "prof": (10000, 20000), "mid": (100, 1000)}[args.workload]
+    if args.workload == "knn":
+        full = wl["factory"](args.seed)
+        inst_n, inst_m = full.n, full.m
+    else:
+        inst_n, inst_m = {"large": (10000, 100000), "prof": (10000, 20000), "mid": (100, 1000)}[args.workload]
     sample = wl["sample"](args.seed)
     if args.workload == "large" and args.steps + args.warmup > 60:
         sample = I.large(args.seed, n=500)
@@ -533,7 +552,15 @@ def main():
     ap.add_argument("--window", type=float, default=5.0, help="served: arrival window (s)")
     ap.add_argument("--pool", type=int, default=6, help="served: networks per size")
     ap.add_argument("--drain-limit", dest="drain_limit", type=float, default=60.0)
+    ap.add_argument("--knn-n", dest="knn_n", type=int, default=1000, help="knn: nodes")
+    ap.add_argument("--knn-q", dest="knn_q", type=int, default=10, help="knn: neighbours")
     args = ap.parse_args()
+    WORKLOADS["knn"] = dict(
+        factory=lambda seed: knn_connected(args.knn_n, args.knn_q, seed),
+        sample=lambda seed: knn_connected(min(args.knn_n, 300), args.knn_q, seed),
+        desc=(f"kNN (Sec. 3.1): n={args.knn_n} uniform points in the unit square, edges both "
+              f"ways to the {args.knn_q} nearest neighbours, log c~U[log 0.5, log 5], "
+              f"log w~U[log 0.3, log 3], u = w log s"))
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     world = int(os.environ.get("WORLD_SIZE", "1"))
