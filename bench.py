@@ -324,10 +324,16 @@ def run_ours(args, rank, world, local_rank):
     if args.ttt:
         with B.Problem(inst) as p3:
             t0 = time.perf_counter()
+            if args.ttt_stop == "paper":
+                eps = args.ttt_eps if args.ttt_eps is not None else \
+                    (0.01 if n <= 1000 else 0.03) / (n * (n - 1.0))
+            else:
+                eps = args.ttt_eps if args.ttt_eps is not None else 1e-4
             r3 = p3.solve(want_T=False, max_iters=args.ttt_max_iters,
-                          **{**common, "stop_mode": "kkt"}, eps=args.ttt_eps, raise_on_error=False)
+                          **{**common, "stop_mode": args.ttt_stop}, eps=eps, raise_on_error=False)
             ttt = {"seconds": time.perf_counter() - t0, "iters": r3["iters"],
-                   "rel_kkt": r3["rel_kkt"], "eps": args.ttt_eps, "status": r3["rc"]}
+                   "rel_kkt": r3["rel_kkt"], "r_over_nm": r3["r_over_nm"], "stop": args.ttt_stop,
+                   "eps": eps, "status": r3["rc"]}
 
     if rank != 0:
         return
@@ -544,7 +550,10 @@ def main():
     ap.add_argument("--compensated-duals", dest="compensated_duals", type=int, default=1,
                     help="FP32 head + BF16 tail duals (1, the library default) or plain FP32 (0)")
     ap.add_argument("--ttt", action="store_true", help="also time a solve to --ttt-eps")
-    ap.add_argument("--ttt-eps", dest="ttt_eps", type=float, default=1e-4)
+    ap.add_argument("--ttt-eps", dest="ttt_eps", type=float, default=None,
+                    help="kkt: relative KKT target (default 1e-4); paper: epsilon of r < n m eps "
+                         "(default 0.01/(n(n-1)) for n <= 1000, 0.03/(n(n-1)) above, Sec. 3.1)")
+    ap.add_argument("--ttt-stop", dest="ttt_stop", default="kkt", choices=["kkt", "paper"])
     ap.add_argument("--ttt-max-iters", dest="ttt_max_iters", type=int, default=20000)
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
     ap.add_argument("--no-e2e", dest="no_e2e", action="store_true")

@@ -165,6 +165,16 @@ int mcf_destroy_problem(mcf_problem* p);
 /* Size queries. */
 int mcf_problem_size(const mcf_problem* p, int32_t* n, int32_t* m);
 
+/* The library's internal node numbering. Relabelling nodes leaves the problem of Sec. 1.1
+ * unchanged. At creation the library renumbers the nodes in reverse Cuthill-McKee order
+ * when that shortens the mean edge span |tail - head| at least 4x, which makes the
+ * per-edge dual-row gathers local in memory. All inputs and outputs stay in the caller's
+ * numbering.
+ *   node_of  NULL, or n int32 (host): node_of[caller node] = internal node
+ * Returns 1 if the nodes were renumbered, 0 if the internal numbering is the caller's
+ * (node_of is then the identity), or a negative error code. */
+int mcf_problem_node_order(const mcf_problem* p, int32_t* node_of);
+
 /* Device bytes one solve of this problem needs at the given precision. */
 int64_t mcf_problem_device_bytes(const mcf_problem* p, int precision);
 

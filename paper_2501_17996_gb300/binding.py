@@ -68,7 +68,8 @@ KERNEL_KINDS = ("edge", "node", "check", "scalar")
 
 SYMBOLS = [
     "mcf_create_problem", "mcf_update_capacities", "mcf_update_weights",
-    "mcf_destroy_problem", "mcf_problem_size", "mcf_problem_device_bytes",
+    "mcf_destroy_problem", "mcf_problem_size", "mcf_problem_node_order",
+    "mcf_problem_device_bytes",
     "mcf_options_default", "mcf_solve", "mcf_solve_timed", "mcf_solve_batch", "mcf_autotune",
     "mcf_submit", "mcf_poll", "mcf_wait",
     "mcf_cancel", "mcf_serving_config", "mcf_project_capped_simplex",
@@ -93,6 +94,7 @@ def _load() -> C.CDLL:
         "mcf_update_weights": (C.c_int, [P, dp]),
         "mcf_destroy_problem": (C.c_int, [P]),
         "mcf_problem_size": (C.c_int, [P, ip, ip]),
+        "mcf_problem_node_order": (C.c_int, [P, ip]),
         "mcf_problem_device_bytes": (C.c_int64, [P, C.c_int]),
         "mcf_options_default": (None, [C.POINTER(mcf_options)]),
         "mcf_solve": (C.c_int, [P, C.POINTER(mcf_options), C.POINTER(mcf_result)]),
@@ -392,6 +394,14 @@ class Problem:
 
     def device_bytes(self, precision="fp32") -> int:
         return mcf_problem_device_bytes(self.h, precision)
+
+    def node_order(self) -> tuple[bool, np.ndarray]:
+        """(renumbered, node_of): node_of[caller node] = the library's internal node."""
+        out = np.empty(self.n, dtype=np.int32)
+        rc = LIB.mcf_problem_node_order(self.h, out.ctypes.data_as(C.POINTER(C.c_int32)))
+        if rc < 0:
+            raise MCFError(rc, "mcf_problem_node_order")
+        return bool(rc), out
 
     def close(self):
         if self.h:

@@ -24,6 +24,11 @@ struct Topology {
   std::vector<int32_t> out_ptr;  // n+1
   std::vector<int32_t> out_idx;  // m internal edge ids, grouped by tail
   int dmax = 0;                  // max in+out degree (Appendix A)
+  // Node renumbering: caller node -> internal node (empty = identity). A relabelling of the
+  // nodes leaves the problem unchanged; e_tail/e_head, in_ptr/out_ptr and every device row
+  // and column use internal numbers, and inputs/outputs are mapped at the boundary.
+  std::vector<int32_t> node_of;
+  int node(int caller) const { return node_of.empty() ? caller : node_of[caller]; }
 };
 
 }  // namespace pdmcf

@@ -200,15 +200,17 @@ static int upload_data(mcf_problem* p, DeviceState* d, cudaStream_t st) {
   std::vector<P> cap(m);
   for (int e = 0; e < m; ++e) cap[e] = (P)p->cap[p->topo.perm[e]];
   CK(cudaMemcpyAsync(d->cap, cap.data(), m * sizeof(P), cudaMemcpyHostToDevice, st));
+  const Topology& tp = p->topo;   // caller (i, j) -> internal row node(j), column node(i)
   std::vector<P> wt((size_t)n * ld, P(0));
   for (int j = 0; j < n; ++j)
     for (int i = 0; i < n; ++i)
-      if (i != j) wt[(size_t)j * ld + i] = (P)p->w[(size_t)i * n + j];
+      if (i != j) wt[(size_t)tp.node(j) * ld + tp.node(i)] = (P)p->w[(size_t)i * n + j];
   CK(cudaMemcpyAsync(d->W, wt.data(), wt.size() * sizeof(P), cudaMemcpyHostToDevice, st));
   if (d->G) {
     for (int j = 0; j < n; ++j)
       for (int i = 0; i < n; ++i)
-        wt[(size_t)j * ld + i] = (i != j) ? (P)p->gamma_mat[(size_t)i * n + j] : P(0.5);
+        wt[(size_t)tp.node(j) * ld + tp.node(i)] =
+            (i != j) ? (P)p->gamma_mat[(size_t)i * n + j] : P(0.5);
     CK(cudaMemcpyAsync(d->G, wt.data(), wt.size() * sizeof(P), cudaMemcpyHostToDevice, st));
   }
   CK(cudaStreamSynchronize(st));   // host staging vectors die at return
@@ -785,6 +787,7 @@ static int solve_t(mcf_problem* p, DeviceState* d, const mcf_options* o, mcf_res
 template <typename P, typename S>
 static int copy_outputs_t(mcf_problem* p, DeviceState* d, mcf_result* res, cudaStream_t st) {
   const int n = d->n, m = d->m;
+  const Topology& tp = p->topo;   // internal row node(j), column node(i) -> caller (i, j)
   const size_t ld = d->ld;
   std::vector<P> buf;
   if (res->T || res->Y) {
@@ -793,13 +796,15 @@ static int copy_outputs_t(mcf_problem* p, DeviceState* d, mcf_result* res, cudaS
       CK(cudaMemcpyAsync(buf.data(), d->That, buf.size() * sizeof(P), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j) res->T[(size_t)i * n + j] = (double)buf[(size_t)j * ld + i];
+        for (int j = 0; j < n; ++j)
+          res->T[(size_t)i * n + j] = (double)buf[(size_t)tp.node(j) * ld + tp.node(i)];
     }
     if (res->Y) {
       CK(cudaMemcpyAsync(buf.data(), d->Yhat, buf.size() * sizeof(P), cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j) res->Y[(size_t)i * n + j] = (double)buf[(size_t)j * ld + i];
+        for (int j = 0; j < n; ++j)
+          res->Y[(size_t)i * n + j] = (double)buf[(size_t)tp.node(j) * ld + tp.node(i)];
     }
   }
   if (res->F) {
@@ -823,7 +828,7 @@ static int copy_outputs_t(mcf_problem* p, DeviceState* d, mcf_result* res, cudaS
     const std::vector<int32_t>& perm = p->topo.perm;
     for (int e2 = 0; e2 < m; ++e2) {
       const int l = perm[e2];
-      for (int i = 0; i < n; ++i) res->F[(size_t)i * m + l] = (double)buf[(size_t)e2 * ld + i];
+      for (int i = 0; i < n; ++i) res->F[(size_t)i * m + l] = (double)buf[(size_t)e2 * ld + tp.node(i)];
     }
   }
   return MCF_OK;

@@ -116,3 +116,22 @@ def test_shape_table(lib):
     for g, v, b, t in shapes:
         assert g in (32, 64, 128, 256, 512, 1024) and b % g == 0 and v >= 1 and t in (0, 1, 2)
     assert {t for *_, t in shapes} == {0, 1, 2}
+
+
+def test_node_renumbering_rule(lib):
+    """kNN networks (Sec. 3.1) get a bandwidth-reducing relabelling; random-chord networks,
+    whose spans it cannot shorten 4x, keep the caller's numbering. The map is a permutation
+    and the mean edge span drops at least 4x when it is used."""
+    from paper_2501_17996_gb300 import instances as I
+    knn = I.knn(400, 6, 0)
+    for inst, expect in ((knn, True), (I.large(0, n=1000), False)):
+        with lib.Problem(inst) as p:
+            renumbered, node_of = p.node_order()
+        assert renumbered == expect, inst.name
+        assert sorted(node_of.tolist()) == list(range(inst.n))
+        span0 = np.abs(inst.tail.astype(np.int64) - inst.head).mean()
+        span1 = np.abs(node_of[inst.tail].astype(np.int64) - node_of[inst.head]).mean()
+        if renumbered:
+            assert 4 * span1 <= span0
+        else:
+            assert np.array_equal(node_of, np.arange(inst.n))

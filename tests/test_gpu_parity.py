@@ -86,6 +86,24 @@ def test_fp64_trajectory_matches_oracle(lib, case):
     assert np.all(np.diag(g["Y"]) == 0)
 
 
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("fp32", 1e-4)])
+def test_renumbered_network_matches_oracle(lib, precision, tol):
+    """A kNN network (Sec. 3.1) that the library renumbers internally: T, Y^ and F, mapped
+    back to the caller's numbering, follow the oracle's trajectory."""
+    inst = I.knn(400, 6, 0)
+    K = 100
+    ref = oracle_k(inst, K, 25)
+    with lib.Problem(inst) as p:
+        assert p.node_order()[0]
+        g = p.solve(precision=precision, stop_mode="none", max_iters=K, k_check=25,
+                    want_T=True, want_F=True, want_Y=True)
+    m = off(inst.n)
+    assert rel_err(g["T"], ref.T, m) < tol
+    assert rel_err(g["Y"], ref.Yhat, m) < tol
+    assert rel_err(g["F"], ref.Fhat) < tol
+    assert np.all(np.diag(g["Y"]) == 0)
+
+
 def test_adaptation_stop_matches_oracle(lib):
     """The stop of the omega adaptation (Sec. 2.4) is taken on the device at the same check
     as in the oracle, and the FP64 trajectories agree past it."""
