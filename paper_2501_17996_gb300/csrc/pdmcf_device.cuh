@@ -148,6 +148,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
+// Bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned source) into L2: a hint with
+// no completion to wait for and no destination in this CTA.
+__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -163,6 +169,8 @@ template <int GROUP> struct GroupScratch {
   double s[2][NW];
   int c[2][NW];
   double x[2][NW];
+  float sf[2][NW];   // FP32 partials stay FP32: a double round trip would run on the FP64 pipe
+  float xf[2][NW];
 };
 
 // Cross-warp stage of a block-wide group reduction: lane l < NW of every warp loads warp
@@ -187,9 +195,16 @@ __device__ __forceinline__ void group_sum_count(P& s, int& c, GroupScratch<GROUP
   if constexpr (GROUP > 32) {
     constexpr int NW = GROUP / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) { sh.s[phase][warp] = (double)s; sh.c[phase][warp] = c; }
-    __syncthreads();
-    P ps = lane < NW ? (P)sh.s[phase][lane] : P(0);
+    P ps;
+    if constexpr (std::is_same<P, float>::value) {
+      if (lane == 0) { sh.sf[phase][warp] = s; sh.c[phase][warp] = c; }
+      __syncthreads();
+      ps = lane < NW ? sh.sf[phase][lane] : 0.f;
+    } else {
+      if (lane == 0) { sh.s[phase][warp] = (double)s; sh.c[phase][warp] = c; }
+      __syncthreads();
+      ps = lane < NW ? (P)sh.s[phase][lane] : P(0);
+    }
     int pc = lane < NW ? sh.c[phase][lane] : 0;
     s = cross_warp<NW>(ps, P(0), [](P a, P b) { return a + b; });
     c = cross_warp<NW>(pc, 0, [](int a, int b) { return a + b; });
@@ -204,9 +219,16 @@ __device__ __forceinline__ P group_max(P v, GroupScratch<GROUP>& sh, int& phase)
   if constexpr (GROUP > 32) {
     constexpr int NW = GROUP / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) sh.x[phase][warp] = (double)v;
-    __syncthreads();
-    P pv = lane < NW ? (P)sh.x[phase][lane] : (P)(-INFINITY);
+    P pv;
+    if constexpr (std::is_same<P, float>::value) {
+      if (lane == 0) sh.xf[phase][warp] = v;
+      __syncthreads();
+      pv = lane < NW ? sh.xf[phase][lane] : -INFINITY;
+    } else {
+      if (lane == 0) sh.x[phase][warp] = (double)v;
+      __syncthreads();
+      pv = lane < NW ? (P)sh.x[phase][lane] : (P)(-INFINITY);
+    }
     v = cross_warp<NW>(pv, (P)(-INFINITY), [](P a, P b) { return fmax(a, b); });
     phase ^= 1;
   }
@@ -624,6 +646,17 @@ edge_kernel(IterArgs<P, S> a) {
       nc = a.cap[e + ngroups];
       nmu = a.mu[e + ngroups];
       nmul = a.mu_lo[e + ngroups];
+      // and its rows into L2 while this edge is projected (rows are 16-byte aligned and
+      // ld * element size is a multiple of 16)
+      if (lane == 0) {
+        prefetch_l2(Fo + (size_t)(e + ngroups) * a.ld, (uint32_t)(a.ld * sizeof(S)));
+        prefetch_l2(Y + (size_t)nt * a.ld, (uint32_t)(a.ld * sizeof(P)));
+        prefetch_l2(Y + (size_t)nh * a.ld, (uint32_t)(a.ld * sizeof(P)));
+        if (ylo) {
+          prefetch_l2(ylo + (size_t)nt * a.ld, (uint32_t)(a.ld * 2));
+          prefetch_l2(ylo + (size_t)nh * a.ld, (uint32_t)(a.ld * 2));
+        }
+      }
     }
     const S* fo = Fo + (size_t)e * a.ld;
     const P* yh = Y + (size_t)h * a.ld;
