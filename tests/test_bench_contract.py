@@ -1,0 +1,57 @@
+"""bench.py on the CPU: the reference arm's JSON line (the oracle timed on host cores) and the
+algorithmic-byte model used for the roofline."""
+import importlib.util
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench_module():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_reference_arm_prints_one_contract_line():
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "mid",
+                          "--steps", "2", "--warmup", "3"], cwd=ROOT, capture_output=True,
+                         text=True, timeout=600, check=True).stdout.strip().splitlines()
+    assert len(out) == 1
+    line = json.loads(out[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 3
+    assert line["value"] > 0 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["config"]["n"] == 100 and line["config"]["m"] == 1000
+
+
+def test_algorithmic_bytes_model():
+    b = _bench_module()
+    n, m = 10000, 100000
+    a0 = b.algorithmic_bytes(n, m, 4, 4, kind=0)
+    a2 = b.algorithmic_bytes(n, m, 4, 4, kind=2)
+    assert a0["edge"] == 2 * 4 * n * m + 4 * n * n + 16 * m
+    assert a0["node"] == 4 * n * m + 5 * 4 * n * n + 4 * (m + 2 * n)
+    assert a2["edge"] - a0["edge"] == 4 * n * n and a2["node"] - a0["node"] == 4 * n * n
+    assert a0["iteration_floor"] == 2 * 4 * n * m + 3 * 4 * n * n
+
+
+def test_knn_workload_is_strongly_connected():
+    import numpy as np
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+
+    b = _bench_module()
+    inst = b.knn_connected(300, 10, 0)
+    g = sp.coo_matrix((np.ones(inst.m), (inst.tail, inst.head)), shape=(inst.n, inst.n))
+    assert connected_components(g, directed=True, connection="strong")[0] == 1
+    assert set(zip(inst.tail.tolist(), inst.head.tolist())) == \
+        set(zip(inst.head.tolist(), inst.tail.tolist()))   # edges both ways (Sec. 3.1)
