@@ -312,12 +312,12 @@ def pdmcf(n, tail, head, cap, kind, w, gamma=None, *, eps=1e-6, stop_mode="kkt",
     "none" runs exactly max_iters iterations. Initialisation F^{-1/2} = 0,
     Y^0 = I - 1 1^T, omega^0 = 1 (Sec. 2.5) unless a warm start is given.
 
-    omega stops adapting from iteration omega_freeze_iter on, and (adapt_guard > 0) in the
-    final phase: it begins at the first stop test with a finite rel_kkt below
-    adapt_guard_below (omega_arm = omega then); in it omega stops adapting from the
-    iteration after a stop test whose finite rel_kkt exceeds adapt_guard times the smallest
-    one so far, or where omega has moved more than a factor adapt_guard away from
-    omega_arm. Sec. 2.4 allows ending the adaptation after some iterations, a constant omega
+    omega stops adapting from iteration omega_freeze_iter on, and (adapt_guard > 0, written
+    g) from the iteration after a stop test where omega is more than a factor g^2 away from
+    omega_ref (omega at the first stop test with a finite rel_kkt), or, in the final phase,
+    which begins at the first stop test with rel_kkt below adapt_guard_below (omega_arm =
+    omega then), where omega is more than a factor g away from omega_arm or a finite
+    rel_kkt exceeds g times the smallest one so far. Sec. 2.4 allows ending the adaptation after some iterations, a constant omega
     keeping the convergence proof; the guard is the point it is applied at (the rule of
     Eq. e-primal_weight can run away: omega -> 0 or infinity). adapt_guard = 0 is the
     adaptation without that stop.
@@ -339,6 +339,7 @@ def pdmcf(n, tail, head, cap, kind, w, gamma=None, *, eps=1e-6, stop_mode="kkt",
     Fhat = Yhat = mu = None
     hist = []
     best_kkt = math.inf
+    omega_ref = 0.0
     omega_arm = 0.0
     status = "max_iters"
     k = 0
@@ -373,14 +374,22 @@ def pdmcf(n, tail, head, cap, kind, w, gamma=None, *, eps=1e-6, stop_mode="kkt",
         if (k + 1) % k_check == 0 or k + 1 >= max_iters:
             met = metrics(Fhat, Yhat, Q, A, c, util)
             r = met.r
-            if adapt_guard > 0 and math.isfinite(met.rel_kkt):
-                if omega_arm > 0 and (omega_freeze_iter < 0 or omega_freeze_iter > k + 1) and \
-                        (met.rel_kkt > adapt_guard * best_kkt or omega > adapt_guard * omega_arm
-                         or omega * adapt_guard < omega_arm):
+            if adapt_guard > 0:
+                fin = math.isfinite(met.rel_kkt)
+                g2 = adapt_guard * adapt_guard
+                drift_ref = omega_ref > 0 and (omega > g2 * omega_ref or omega * g2 < omega_ref)
+                final_phase = omega_arm > 0 and ((fin and met.rel_kkt > adapt_guard * best_kkt)
+                                                 or omega > adapt_guard * omega_arm
+                                                 or omega * adapt_guard < omega_arm)
+                if (drift_ref or final_phase) and \
+                        (omega_freeze_iter < 0 or omega_freeze_iter > k + 1):
                     omega_freeze_iter = k + 1
-                best_kkt = min(best_kkt, met.rel_kkt)
-                if omega_arm == 0 and best_kkt < adapt_guard_below:
-                    omega_arm = omega
+                if fin:
+                    best_kkt = min(best_kkt, met.rel_kkt)
+                    if omega_ref == 0:
+                        omega_ref = omega
+                    if omega_arm == 0 and best_kkt < adapt_guard_below:
+                        omega_arm = omega
             if history:
                 hist.append(dict(k=k + 1, omega=omega, r=r, rel_kkt=met.rel_kkt,
                                  rel_gap=met.rel_gap, rel_cons=met.rel_cons,

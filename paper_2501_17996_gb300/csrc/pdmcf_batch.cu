@@ -230,6 +230,7 @@ int BatchEngine::add(mcf_problem* p, const mcf_options& o, void* tag, int* slot_
   d.freeze = o.omega_freeze_iter;
   d.guard = o.adapt_guard;
   d.guard_below = o.adapt_guard_below;
+  d.omega_ref = 0.0;
   d.omega_arm = 0.0;
   d.best_kkt = INFINITY;
   d.r = INFINITY;

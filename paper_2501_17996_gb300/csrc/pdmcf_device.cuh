@@ -475,17 +475,26 @@ static __device__ __forceinline__ void scalar_update(DevScalars* s, double dF2, 
     s->omega = pow(dY / dF, s->theta) * pow(s->omega, 1.0 - s->theta);
   }
   // Sec. 2.4: omega may stop adapting after some iterations (a constant omega keeps the
-  // convergence proof). The final phase begins at the first check with a finite measure
-  // below guard_below (omega_arm records omega then); in it, omega stops adapting from the
-  // next iteration once the measure exceeds guard x its best or omega has moved more than
-  // a factor guard away from omega_arm.
-  if (check && s->guard > 0.0 && isfinite(s->rel_kkt)) {
-    if (s->omega_arm > 0.0 && (s->freeze < 0 || s->freeze > k + 1) &&
-        (s->rel_kkt > s->guard * s->best_kkt || s->omega > s->guard * s->omega_arm ||
-         s->omega * s->guard < s->omega_arm))
-      s->freeze = k + 1;
-    if (s->rel_kkt < s->best_kkt) s->best_kkt = s->rel_kkt;
-    if (s->omega_arm == 0.0 && s->best_kkt < s->guard_below) s->omega_arm = s->omega;
+  // convergence proof). omega_ref records omega at the first check with a finite measure,
+  // omega_arm at the first one with a measure below guard_below (the final phase). At every
+  // later check, omega stops adapting from the next iteration once it leaves a factor
+  // guard^2 of omega_ref, or, in the final phase, once it leaves a factor guard of
+  // omega_arm or a finite measure exceeds guard x its best.
+  if (check && s->guard > 0.0) {
+    const bool fin = isfinite(s->rel_kkt);
+    const double g2 = s->guard * s->guard;
+    const bool drift_ref = s->omega_ref > 0.0 &&
+                           (s->omega > g2 * s->omega_ref || s->omega * g2 < s->omega_ref);
+    const bool final_phase = s->omega_arm > 0.0 &&
+                             ((fin && s->rel_kkt > s->guard * s->best_kkt) ||
+                              s->omega > s->guard * s->omega_arm ||
+                              s->omega * s->guard < s->omega_arm);
+    if ((drift_ref || final_phase) && (s->freeze < 0 || s->freeze > k + 1)) s->freeze = k + 1;
+    if (fin) {
+      if (s->rel_kkt < s->best_kkt) s->best_kkt = s->rel_kkt;
+      if (s->omega_ref == 0.0) s->omega_ref = s->omega;
+      if (s->omega_arm == 0.0 && s->best_kkt < s->guard_below) s->omega_arm = s->omega;
+    }
   }
   s->alpha = s->eta / s->omega;
   s->beta = s->eta * s->omega;

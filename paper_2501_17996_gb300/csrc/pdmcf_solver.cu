@@ -678,6 +678,7 @@ static int solve_t(mcf_problem* p, DeviceState* d, const mcf_options* o, mcf_res
   h.freeze = o->omega_freeze_iter;
   h.guard = o->adapt_guard;
   h.guard_below = o->adapt_guard_below;
+  h.omega_ref = 0.0;
   h.omega_arm = 0.0;
   h.best_kkt = INFINITY;
   h.r = INFINITY;

@@ -20,7 +20,7 @@ struct DevScalars {
   // primal weight rule parameters
   double theta, tau;
   long long k_adapt, freeze;
-  double guard, guard_below, best_kkt, omega_arm;   // the adaptation stop (see scalar_update)
+  double guard, guard_below, best_kkt, omega_ref, omega_arm;   // adaptation stop (scalar_update)
   // results of the last check iteration; check_k = k after that iteration
   long long check_k;
   double r, P, D, g_norm, rel_gap, rel_cons, rel_stat, rel_kkt, nonpos_frac;

@@ -410,14 +410,21 @@ def test_adaptation_stop_keeps_omega_constant():
     # the final phase begins at the first check with rel_kkt below 1e-2 (omega_arm = omega
     # there); the stop follows the first later check whose measure is above 1.05 x the best
     # before it or whose omega is more than a factor 1.05 away from omega_arm
-    best, arm, trigger = math.inf, 0.0, None
+    # (omega_ref: omega at the first finite measure; the stop also follows a check whose
+    # omega is more than a factor 1.05^2 away from it)
+    best, ref, arm, trigger = math.inf, 0.0, 0.0, None
     for h in free.history:
-        if trigger is None and arm > 0 and (h["rel_kkt"] > 1.05 * best or h["omega"] > 1.05 * arm
-                                            or h["omega"] * 1.05 < arm):
+        fin, w = math.isfinite(h["rel_kkt"]), h["omega"]
+        if trigger is None and ((ref > 0 and (w > 1.05 ** 2 * ref or w * 1.05 ** 2 < ref)) or
+                                (arm > 0 and ((fin and h["rel_kkt"] > 1.05 * best)
+                                              or w > 1.05 * arm or w * 1.05 < arm))):
             trigger = h["k"]
-        best = min(best, h["rel_kkt"])
-        if arm == 0 and best < 1e-2:
-            arm = h["omega"]
+        if fin:
+            best = min(best, h["rel_kkt"])
+            if ref == 0:
+                ref = w
+            if arm == 0 and best < 1e-2:
+                arm = w
     assert trigger is not None and held.omega_frozen_at == trigger
     for a, b in zip(free.history, held.history):
         if a["k"] <= trigger:
