@@ -135,3 +135,35 @@ def test_node_renumbering_rule(lib):
             assert 4 * span1 <= span0
         else:
             assert np.array_equal(node_of, np.arange(inst.n))
+
+
+def test_readme_c_example_compiles_and_runs(lib, tmp_path):
+    """The C example of README.md, built against include/pdmcf.h and libpdmcf.so: without a
+    GPU the solve reports MCF_ERR_CUDA; with one it returns the two-node closed form
+    (T_10 = c_a = 2, T_01 = c_b = 3, Sec. 1.1)."""
+    import shutil
+    import subprocess
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    readme = open(os.path.join(root, "README.md")).read()
+    code = re.search(r"```c\n(.*?)```", readme, re.S).group(1)
+    src = tmp_path / "example.c"
+    src.write_text(code)
+    from paper_2501_17996_gb300 import build as _build
+
+    libdir = os.path.dirname(_build.LIB_PATH)
+    exe = tmp_path / "example"
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(root, "include"),
+                    str(src), "-o", str(exe), "-L", libdir, "-lpdmcf", f"-Wl,-rpath,{libdir}"],
+                   check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stdout + out.stderr
+    if "iters=" in out.stdout:
+        t10 = float(re.search(r"T10=([\d.]+)", out.stdout).group(1))
+        t01 = float(re.search(r"T01=([\d.]+)", out.stdout).group(1))
+        assert abs(t10 - 2.0) < 1e-3 and abs(t01 - 3.0) < 1e-3
+    else:
+        assert not HAS_GPU and "solve: -4" in out.stdout
