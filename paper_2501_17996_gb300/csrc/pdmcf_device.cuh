@@ -142,10 +142,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Returns false if the phase did not complete within the bound.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Returns false if the phase did not complete within 2^22 polls or 2 s, whichever comes first
+// (a poll may suspend for a system-dependent time, so the deadline bounds the wall clock).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < (1u << 22); ++it)
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 0; it < (1u << 22); ++it) {
     if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > 2000000000ull) return false;
+  }
   return false;
 }
 // Bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned source) into L2: a hint with
