@@ -189,6 +189,32 @@ def oracle_iters_per_s(sample, k_check: int, steps: int, warmup: int):
     return steps / dt, dt
 
 
+def host_description() -> str:
+    """nproc and the CPU model of this host (the oracle's timing context)."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in ([] if model else open("/proc/cpuinfo")):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu model", "hardware") and ":" in line:
+                model = line.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    if not model:
+        import platform
+
+        model = platform.machine()
+    return f"{os.cpu_count()} host cores, {model}"
+
+
 def cpu_baseline(wl, inst, seed, k_check, steps=20, warmup=1):
     sample = wl["sample"](seed)
     ips, dt = oracle_iters_per_s(sample, k_check, steps, warmup)
@@ -198,6 +224,7 @@ def cpu_baseline(wl, inst, seed, k_check, steps=20, warmup=1):
         "unit": "iters/s",
         "cores": 1,
         "kind": "oracle",
+        "host": host_description(),
         "sample": (f"{steps} FP64 oracle iterations (single-threaded numpy/scipy) on the same "
                    f"recipe at n={sample.n}, m={sample.m} ({dt:.1f} s), scaled by "
                    f"n m ratio {scale:.3g} to the full workload"),
@@ -229,6 +256,7 @@ def run_reference(args, rank, world):
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: {wl['desc']}", "n": inst_n, "m": inst_m},
         "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle",
+                         "host": host_description(),
                          "sample": (f"each step one FP64 oracle iteration on the same recipe at "
                                     f"n={sample.n}, m={sample.m}; {args.steps} steps took "
                                     f"{dt:.1f} s; scaled by n m ratio {scale:.3g}")},
