@@ -113,6 +113,7 @@ struct DeviceState {
   int requested_shape = -1;   // mcf_options.shape the grids were configured for
   // pipelined edge phase (tma >= 0): one CTA per SM over head-aligned edge ranges
   int tma = -1, tma_kind = 0, grid_tma = 0, grid_node_pin = 0;   // kind 1 bulk-copy, 2 in-sum
+  bool renumbered = false;   // nodes relabelled for locality (Topology::node_of)
   size_t tma_smem = 0;
   void* Pin = nullptr;
   int32_t* cta_ptr = nullptr;
@@ -240,9 +241,16 @@ static int setup_tma(DeviceState* d, int want) {
   int t = -1, kind = 0;
   if (want >= NUM_SHAPES + NUM_TMA) { t = want - NUM_SHAPES - NUM_TMA; kind = 2; }
   else if (want >= NUM_SHAPES) { t = want - NUM_SHAPES; kind = 1; }
-  // automatic choice: the register shapes (kind 0), measured fastest at n = 10^4, m = 10^5
-  // (edge + node 6.0 ms against 6.1 ms for kind 2 and 7.7 ms for kind 1); mcf_autotune
-  // times every kind on the caller's problem
+  // automatic choice, measured at n = 10^4 (FP32): on networks without node locality
+  // (random chords, m = 10^5) the in-sum kind saves the node phase's second read of each F
+  // row (edge + node 4.69 ms against 4.83 ms for the register kind); on renumbered networks
+  // (kNN) the register kind's gathers hit L2 and it wins (4.67 against 4.97 ms). mcf_autotune
+  // times every kind on the caller's problem.
+  else if (want < 0 && std::is_same<S, float>::value && !d->renumbered &&
+           (size_t)d->ld * sizeof(float) >= 8192 && 2 * (smem2 + 4096) <= (size_t)smem_optin) {
+    for (int c = 0; c < NUM_TMA && t < 0; ++c)
+      if (kTmaVpt[c] * TMA_BLOCK >= nchunks) { t = c; kind = 2; }
+  }
   if (t < 0) { d->tma = -1; d->tma_kind = 0; d->grid_tma = 0; return MCF_OK; }
   if (kTmaVpt[t] * TMA_BLOCK < nchunks) {
     set_error("shape too small for this problem");
@@ -381,6 +389,7 @@ static int alloc_state(mcf_problem* p, int precision, int device, int shape, cud
   DeviceState* d = new DeviceState();
   d->device = device;
   d->precision = precision;
+  d->renumbered = !p->topo.node_of.empty();
   d->n = p->n;
   d->m = p->m;
   d->ld = (int)ld_of(p->n);
