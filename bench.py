@@ -85,11 +85,18 @@ def peaks():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the CUDA sources with comments and whitespace removed: it changes when the
+    code changes, not when its comments do."""
+    import re
+
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2501_17996_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
         if f.endswith((".cuh", ".cu", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+            text = open(os.path.join(csrc, f), encoding="utf-8").read()
+            text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+            text = re.sub(r"//[^\n]*", " ", text)
+            h.update(f.encode() + b"\0" + " ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -10,14 +10,18 @@
 // Pad entries i in [n, ld) are zero in every array and stay zero.
 //
 // One iteration k (Eq. e-pdhg-step, Algorithm 2.1 step 2) is three launches:
-//   edge_kernel   per edge l: q = f + alpha (Y_{:,head} - Y_{:,tail}), mu by Newton on
-//                 phi(mu) = sum (q - mu)_+ - c (the capped-simplex projection of Sec. 2.3),
-//                 f^ = (q - mu)_+, f_new = rho f^ + (1 - rho) f; FP64 partial of ||dF||^2.
+//   edge_kernel   per edge l: q = f + alpha (Y_{:,head} - Y_{:,tail}), formed relative to the
+//                 previous multiplier; mu by Newton on phi(mu) = sum (q - mu)_+ - c (the
+//                 capped-simplex projection of Sec. 2.3), f^ = (q - mu)_+,
+//                 f_new = rho f^ + (1 - rho) f; ||dF||^2 (FP32 per thread, FP64 across).
+//                 Variants: edge_insum_kernel (in-sums of F^{k+1/2} per head, so the node
+//                 phase gathers out-edges only) and edge_tma_kernel (bulk-copy pipeline).
 //   node_kernel   per node j: p = sum_{in(j)} f_new - sum_{out(j)} f_new = (F^{k+1/2}A^T)_{:,j},
 //                 F^ A^T = (p - (1-rho) P_old)/rho, F^{k+1} A^T = 2 F^ A^T - P_old,
 //                 v = Y_{:,j} - beta F^{k+1}A^T, Y^ = prox(v) (0 at i = j),
-//                 Y_new = rho Y^ + (1 - rho) Y; FP64 partial of ||dY||^2 and, on check
-//                 iterations, the objective/conjugate/consistency partials.
+//                 Y_new = rho Y^ + (1 - rho) Y (head FP32 + tail BF16 for FP32 iterates);
+//                 ||dY||^2 and, in the check variant, the objective/conjugate/consistency
+//                 partials.
 //   scalar_kernel one block: fixed-order FP64 reductions, the primal weight rule of
 //                 Eq. (e-primal_weight), alpha/beta for the next iteration and, on check
 //                 iterations, r (Eq. e-res), the duality gap and the relative KKT measure.
