@@ -167,3 +167,30 @@ def test_readme_c_example_compiles_and_runs(lib, tmp_path):
         assert abs(t10 - 2.0) < 1e-3 and abs(t01 - 3.0) < 1e-3
     else:
         assert not HAS_GPU and "solve: -4" in out.stdout
+
+
+def test_renumbering_recovers_grid_locality(lib):
+    """A 30 x 30 grid (edges both ways) with shuffled node labels: reverse Cuthill-McKee must
+    bring the mean edge span back to the order of the grid side (30), from ~n/3 = 300."""
+    rng = np.random.default_rng(0)
+    side = 30
+    n = side * side
+    label = rng.permutation(n)
+    tail, head = [], []
+    for r in range(side):
+        for c in range(side):
+            v = r * side + c
+            for dr, dc in ((0, 1), (1, 0)):
+                if r + dr < side and c + dc < side:
+                    u = (r + dr) * side + (c + dc)
+                    tail += [label[v], label[u]]
+                    head += [label[u], label[v]]
+    tail = np.array(tail, np.int32)
+    head = np.array(head, np.int32)
+    w = np.ones((n, n))
+    inst = I.Instance(n, tail, head, np.ones(len(tail)), "log", w, None, "grid")
+    with lib.Problem(inst) as p:
+        renumbered, node_of = p.node_order()
+    assert renumbered
+    span = np.abs(node_of[tail].astype(np.int64) - node_of[head]).mean()
+    assert span <= 2 * side, span
