@@ -432,3 +432,18 @@ def test_adaptation_stop_keeps_omega_constant():
         else:
             assert b["omega"] == held.history[trigger // 50 - 1]["omega"]
     assert free.omega != held.omega
+
+
+def test_warm_start_continues_the_iteration():
+    """Reading of Sec. 3.1's warm start: restarting from (F^{k-1/2}, Y^k, omega) with k reset to
+    0 continues the iteration exactly when the restart falls on a multiple of k_adapt (the
+    primal-weight updates then land on the same iterations)."""
+    inst = I.mid(1)
+    args = (inst.n, inst.tail, inst.head, inst.cap, inst.kind, inst.w, inst.gamma)
+    kw = dict(stop_mode="none", k_check=50, adapt_guard=0)
+    straight = O.pdmcf(*args, max_iters=500, **kw)
+    first = O.pdmcf(*args, max_iters=300, **kw)
+    second = O.pdmcf(*args, max_iters=200, F0=first.F, Y0=first.Y, omega0=first.omega, **kw)
+    assert second.omega == straight.omega
+    assert np.array_equal(second.T, straight.T)
+    assert np.array_equal(second.Yhat, straight.Yhat)
