@@ -98,12 +98,16 @@ typedef struct mcf_options {
   int     shape;             /* kernel launch shape index (-1 = automatic); see
                                 mcf_shape_info. Lets tests and the tuner pick any shape
                                 whose capacity covers the problem                          */
-  double  adapt_guard;       /* stop adapting omega (keep it constant, Sec. 2.4) from the
-                                iteration after a stop test whose finite relative KKT
-                                measure exceeds adapt_guard x the smallest one of this
-                                solve, once that smallest one is below adapt_guard_below;
-                                0 = adapt throughout (default 10)                          */
-  double  adapt_guard_below; /* see adapt_guard (default 1e-2)                             */
+  double  adapt_guard;       /* g: stop adapting omega (keep it constant, Sec. 2.4) from
+                                the iteration after a stop test where omega is more than a
+                                factor g^2 away from its value at the first stop test with
+                                a finite relative KKT measure, or, once that measure has
+                                been below adapt_guard_below (the final phase), where omega
+                                is more than a factor g away from its value when that phase
+                                began or a finite measure exceeds g x the smallest one of
+                                the solve. 0 = adapt throughout (default 10). The result
+                                reports the iteration in omega_frozen_at.                  */
+  double  adapt_guard_below; /* start of the final phase for adapt_guard (default 1e-2)   */
 } mcf_options;
 
 /* ---------------------------------------------------------------- results */
