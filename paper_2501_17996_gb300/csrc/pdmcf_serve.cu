@@ -1,4 +1,4 @@
-// pdmcf_serve.cpp — asynchronous solves with continuous batching
+// pdmcf_serve.cu — asynchronous solves with continuous batching
 // (mcf_submit / mcf_poll / mcf_wait / mcf_cancel / mcf_serving_config).
 //
 // A scheduler thread owns one BatchEngine per device. Between chunks of batched PDHG
