@@ -447,3 +447,27 @@ def test_warm_start_continues_the_iteration():
     assert second.omega == straight.omega
     assert np.array_equal(second.T, straight.T)
     assert np.array_equal(second.Yhat, straight.Yhat)
+
+
+def test_duality_gap_bounds_the_traffic_error():
+    """Log utility: u = w log s is strongly concave with modulus >= w_min / T_max^2 on the
+    segment between a feasible T and the optimum T*, and U(T*) <= D (weak duality), so
+    |T_ij - T*_ij| <= T_max sqrt(2 (D - U(T)) / w_min). The oracle's dual bound and its T
+    must satisfy this at every stopping point; a dual bound too low would violate it."""
+    inst = I.tiny(0)
+    n = inst.n
+    off = offdiag(n)
+    Tstar = np.load(os.path.join(GOLDEN, "oracle_tiny_s0.npz"))["T"]
+    wmin = inst.w[off].min()
+    checked = 0
+    for iters in (100, 300, 1000, 3000):
+        r = solve(inst, stop_mode="none", max_iters=iters)
+        if not r.metrics.feasible:
+            continue
+        gap = r.metrics.D - r.metrics.P
+        assert gap >= -1e-12 * abs(r.metrics.D)
+        tmax = max(r.T[off].max(), Tstar[off].max())
+        bound = tmax * math.sqrt(2.0 * max(gap, 0.0) / wmin)
+        assert np.abs(r.T[off] - Tstar[off]).max() <= bound * (1 + 1e-9) + 1e-12
+        checked += 1
+    assert checked >= 3
