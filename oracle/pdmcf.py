@@ -305,7 +305,7 @@ class Result:
 def pdmcf(n, tail, head, cap, kind, w, gamma=None, *, eps=1e-6, stop_mode="kkt",
           max_iters=100000, rho=1.9, theta=0.5, k_adapt=100, tau=1e-5,
           omega_freeze_iter=-1, k_check=1, F0=None, Y0=None, omega0=1.0,
-          adapt_guard=10.0, adapt_guard_below=1e-2, history=False) -> Result:
+          adapt_guard=10.0, adapt_guard_below=1e-2, history=False, on_check=None) -> Result:
     """Algorithm 2.1 (PDMCF), float64.
 
     stop_mode: "paper" stops when r^k < n m eps (Sec. 2.5), "kkt" when rel_kkt^k < eps,
@@ -321,6 +321,9 @@ def pdmcf(n, tail, head, cap, kind, w, gamma=None, *, eps=1e-6, stop_mode="kkt",
     keeping the convergence proof; the guard is the point it is applied at (the rule of
     Eq. e-primal_weight can run away: omega -> 0 or infinity). adapt_guard = 0 is the
     adaptation without that stop.
+
+    on_check, if given, is called with the record of every stop test (the same dict that
+    ``history`` collects); it observes the run and changes nothing in it.
     """
     tail = np.asarray(tail, dtype=np.int64)
     head = np.asarray(head, dtype=np.int64)
@@ -390,11 +393,15 @@ def pdmcf(n, tail, head, cap, kind, w, gamma=None, *, eps=1e-6, stop_mode="kkt",
                         omega_ref = omega
                     if omega_arm == 0 and best_kkt < adapt_guard_below:
                         omega_arm = omega
-            if history:
-                hist.append(dict(k=k + 1, omega=omega, r=r, rel_kkt=met.rel_kkt,
-                                 rel_gap=met.rel_gap, rel_cons=met.rel_cons,
-                                 rel_stat=met.rel_stat, P=met.P, D=met.D,
-                                 nonpos_frac=met.nonpos_frac))
+            if history or on_check is not None:
+                rec = dict(k=k + 1, omega=omega, r=r, rel_kkt=met.rel_kkt,
+                           rel_gap=met.rel_gap, rel_cons=met.rel_cons,
+                           rel_stat=met.rel_stat, P=met.P, D=met.D,
+                           nonpos_frac=met.nonpos_frac)
+                if history:
+                    hist.append(rec)
+                if on_check is not None:
+                    on_check(rec)
         F, Y = F_new, Y_new
         k += 1
     if Fhat is None:

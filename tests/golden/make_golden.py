@@ -21,11 +21,14 @@ CASES = {
     "tiny_s0": (lambda: I.tiny(0), 1e-10, 10),
     "mid_s0": (lambda: I.mid(0), 1e-9, 10),
     "midpow_s0": (lambda: I.large(0, n=100), 1e-9, 10),
-    "slice_s0": (lambda: I.large_slice(0), 1e-7, 10),
+    # the large recipe at n = 1000: a tighter stop brackets the optimum U* between the
+    # primal and dual values (weak duality) to 1e-5 relative
+    "slice_s0_kkt1e-5": (lambda: I.large_slice(0), 1e-5, 50),
     # stopped at the acceptance tolerance with the stop test every 50 iterations, as the
     # GPU solves they are compared with
     "mid_s0_kkt1e-4": (lambda: I.mid(0), 1e-4, 50),
     "midpow_s0_kkt1e-4": (lambda: I.large(0, n=100), 1e-4, 50),
+    "slice_s0_kkt1e-4": (lambda: I.large_slice(0), 1e-4, 50),
 }
 
 
@@ -33,12 +36,24 @@ def make(name: str) -> str:
     factory, tol, k_check = CASES[name]
     inst = factory()
     t0 = time.time()
+
+    def progress(rec):
+        if rec["k"] % 1000 == 0:
+            print(f"  {name} k={rec['k']} omega={rec['omega']:.4g} rel_kkt={rec['rel_kkt']:.3g}",
+                  flush=True)
+
     r = O.pdmcf(inst.n, inst.tail, inst.head, inst.cap, inst.kind, inst.w, inst.gamma,
-                eps=tol, stop_mode="kkt", max_iters=500000, k_check=k_check)
+                eps=tol, stop_mode="kkt", max_iters=500000, k_check=k_check,
+                history=True, on_check=progress)
     path = os.path.join(HERE, f"oracle_{name}.npz")
+    hk = np.array([h["k"] for h in r.history], dtype=np.int64)
+    ho = np.array([h["omega"] for h in r.history])
+    hr = np.array([h["rel_kkt"] for h in r.history])
     np.savez_compressed(path, T=r.T, Yhat=r.Yhat, utility=r.utility, iters=r.iters,
                         rel_kkt=r.metrics.rel_kkt, rel_gap=r.metrics.rel_gap,
-                        status=r.status, omega=r.omega)
+                        P=r.metrics.P, D=r.metrics.D,
+                        status=r.status, omega=r.omega, omega_frozen_at=r.omega_frozen_at,
+                        hist_k=hk, hist_omega=ho, hist_rel_kkt=hr)
     print(f"{name}: {r.status} iters={r.iters} rel_kkt={r.metrics.rel_kkt:.3g} "
           f"U={r.utility:.12g} {time.time() - t0:.1f}s -> {path}", flush=True)
     return path
