@@ -47,7 +47,7 @@ extern "C" {
 #define MCF_ERR_NUMERIC       -5   /* NaN or Inf in the iterates                       */
 #define MCF_ERR_NOT_CONVERGED -6   /* max_iters reached; results are still filled      */
 #define MCF_ERR_TIMEOUT       -7   /* mcf_wait timed out                               */
-#define MCF_ERR_BUSY          -8   /* submission queue full                            */
+#define MCF_ERR_BUSY          -8   /* queue full, or the problem has an outstanding ticket */
 #define MCF_ERR_OOM_BUDGET    -9   /* instance does not fit the serving HBM budget     */
 #define MCF_ERR_CANCELLED    -10   /* ticket cancelled before it completed             */
 
@@ -208,26 +208,46 @@ int mcf_solve_batch(mcf_problem** problems, int count, const mcf_options* opts,
 
 /* Asynchronous solve: enqueue and return a ticket at once. The serving scheduler admits
  * the request when its device footprint fits the HBM budget (mcf_serving_config) and
- * advances it batched with the other resident requests. May return MCF_ERR_BUSY or
- * MCF_ERR_OOM_BUDGET. The options are copied; the problem must stay alive until the
- * ticket completes. */
+ * advances it batched with the other resident requests. The options are copied; the
+ * problem must stay alive until the ticket is collected.
+ * A problem has at most one outstanding ticket, from mcf_submit until the ticket is
+ * collected: by the mcf_poll or mcf_wait that reports its final status, or by mcf_cancel
+ * of a finished ticket. Its outputs are read from the problem's device state at
+ * collection, so until then mcf_submit, mcf_solve, mcf_solve_batch, mcf_autotune,
+ * mcf_update_capacities, mcf_update_weights and mcf_destroy_problem on that problem return
+ * MCF_ERR_BUSY. Also MCF_ERR_BUSY when the queue is full; MCF_ERR_OOM_BUDGET when the
+ * request's footprint alone exceeds the budget. */
 int mcf_submit(mcf_problem* p, const mcf_options* opts, mcf_ticket* ticket);
 
 /* Non-blocking: *status receives MCF_PENDING until the ticket finishes, then its final
- * status, and *res (if not NULL) is filled as by mcf_solve. A finished ticket is released
- * by the first poll that reports it. */
+ * status, and *res (if not NULL) is filled as by mcf_solve. The first poll that reports
+ * the final status collects the ticket (its id is then unknown) and frees the problem for
+ * new work. */
 int mcf_poll(mcf_ticket ticket, int* status, mcf_result* res);
 
 /* Blocking form of mcf_poll with a timeout in milliseconds (< 0: no limit). Returns
  * MCF_ERR_TIMEOUT if the ticket is still pending when the limit passes. */
 int mcf_wait(mcf_ticket ticket, int64_t timeout_ms, int* status, mcf_result* res);
 
-/* Cancel a pending ticket; its poll then reports MCF_ERR_CANCELLED. */
+/* Cancel a ticket. Queued: removed at once. Running in the batched engine: it leaves its
+ * slot at the next chunk boundary (every 10 iterations), keeping the iterate reached as the
+ * problem's warm state. Running one at a time (MCF_FP64, MCF_BF16_F or a forced shape):
+ * it runs to its stop rule. In each case the next poll reports MCF_ERR_CANCELLED and
+ * collects it. Finished but not collected: its result is discarded and the ticket is
+ * collected. */
 int mcf_cancel(mcf_ticket ticket);
 
-/* Serving configuration: HBM budget for admitted requests (bytes) and the maximum number
- * of requests resident at once. Defaults: 120 GB, 256. */
+/* Serving configuration: HBM budget for admitted requests (bytes, > 0) and the maximum
+ * number of requests resident at once (>= 0; 0 pauses admission: requests queue but none
+ * starts). Defaults: 120 GB, 256. */
 int mcf_serving_config(int64_t hbm_budget_bytes, int max_resident);
+
+/* Stop the serving threads. Every ticket not finished ends with MCF_ERR_CANCELLED: queued
+ * ones at once, batched running ones after the chunk in progress (their problems keep
+ * the iterate reached), a running one-at-a-time solve when it returns. Returns when both
+ * threads have exited; their tickets are still collected by mcf_poll / mcf_wait. A later
+ * mcf_submit starts the threads again. Library service; the paper has no counterpart. */
+int mcf_serving_shutdown(void);
 
 /* Per-kernel device times of a timed solve (CUDA events recorded on the solve stream
  * between consecutive kernels). Index 0 edge phase, 1 node phase, 2 residual check,
@@ -269,16 +289,18 @@ int mcf_project_capped_simplex(int32_t n, int32_t m, int32_t ld, const float* Qt
                                const float* cap, float* Ft, float* mu, double* dist2,
                                void* stream);
 
-/* The same projection for callers that cannot allocate device memory: code running while
- * a CUDA graph is being captured, processes whose device memory belongs to their own pool
- * or to a framework allocator, and loops that must never enter the allocator. The paper has
- * no counterpart; this is a library service. Arguments and results are those of
- * mcf_project_capped_simplex, except:
+/* The same projection for callers that cannot allocate device memory: processes whose
+ * device memory belongs to their own pool or to a framework allocator that must see every
+ * allocation, and loops that must never enter the allocator (a cudaMalloc can synchronize
+ * the device and take milliseconds). The paper has no counterpart; this is a library
+ * service. Arguments and results are those of mcf_project_capped_simplex, except:
  *   - no device memory is allocated or freed: the scratch (m + 1 doubles) is a fixed array in
  *     the library image, present on every GPU that loads the library until the process
  *     exits; m is limited to 262144 columns (MCF_ERR_INVALID beyond, nothing launched);
  *   - the first call on each device looks up that array's device address (and may load
- *     the library's device code); make that first call before any stream capture;
+ *     the library's device code); make that first call before any stream capture. The
+ *     address is looked up again when the device's context has changed (for instance after
+ *     a cudaDeviceReset by the application);
  *   - the call returns without synchronizing when dist2 is NULL (the work is queued on
  *     stream); with dist2 it waits for the result;
  *   - all calls share the one array: calls whose work overlaps on the GPU (different

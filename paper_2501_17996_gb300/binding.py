@@ -72,7 +72,7 @@ SYMBOLS = [
     "mcf_problem_device_bytes",
     "mcf_options_default", "mcf_solve", "mcf_solve_timed", "mcf_solve_batch", "mcf_autotune",
     "mcf_submit", "mcf_poll", "mcf_wait",
-    "mcf_cancel", "mcf_serving_config", "mcf_project_capped_simplex",
+    "mcf_cancel", "mcf_serving_config", "mcf_serving_shutdown", "mcf_project_capped_simplex",
     "mcf_project_capped_simplex_noalloc", "mcf_shape_info",
     "mcf_last_error", "mcf_version",
 ]
@@ -109,6 +109,7 @@ def _load() -> C.CDLL:
         "mcf_wait": (C.c_int, [C.c_int64, C.c_int64, C.POINTER(C.c_int), C.POINTER(mcf_result)]),
         "mcf_cancel": (C.c_int, [C.c_int64]),
         "mcf_serving_config": (C.c_int, [C.c_int64, C.c_int]),
+        "mcf_serving_shutdown": (C.c_int, []),
         "mcf_project_capped_simplex": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P, P, P,
                                                  dp, P]),
         "mcf_project_capped_simplex_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P, P,
@@ -344,21 +345,31 @@ def mcf_project_capped_simplex(n: int, m: int, ld: int, Qt_ptr: int, cap_ptr: in
 
 
 def mcf_project_capped_simplex_noalloc(n: int, m: int, ld: int, Qt_ptr: int, cap_ptr: int,
-                                       Ft_ptr: int, mu_ptr: int, stream: int = 0) -> float:
+                                       Ft_ptr: int, mu_ptr: int, stream: int = 0,
+                                       want_dist2: bool = True):
     """As mcf_project_capped_simplex, for callers that cannot allocate device memory (the
-    scratch is a fixed array in the library; m <= 262144). Returns sum ||F - Q||^2."""
+    scratch is a fixed array in the library; m <= 262144). Returns sum ||F - Q||^2, or None
+    with want_dist2=False: then dist2 is passed as NULL and the call returns as soon as the
+    work is queued on `stream`."""
     d2 = C.c_double(0.0)
     rc = LIB.mcf_project_capped_simplex_noalloc(int(n), int(m), int(ld), Qt_ptr, cap_ptr, Ft_ptr,
-                                                mu_ptr, C.byref(d2), stream or None)
+                                                mu_ptr, C.byref(d2) if want_dist2 else None,
+                                                stream or None)
     if rc != MCF_OK:
         raise MCFError(rc, "mcf_project_capped_simplex_noalloc")
-    return d2.value
+    return d2.value if want_dist2 else None
 
 
 def mcf_serving_config(hbm_budget_bytes: int, max_resident: int) -> None:
     rc = LIB.mcf_serving_config(int(hbm_budget_bytes), int(max_resident))
     if rc != MCF_OK:
         raise MCFError(rc, "mcf_serving_config")
+
+
+def mcf_serving_shutdown() -> None:
+    rc = LIB.mcf_serving_shutdown()
+    if rc != MCF_OK:
+        raise MCFError(rc, "mcf_serving_shutdown")
 
 
 # ---------------------------------------------------------------- convenience owner

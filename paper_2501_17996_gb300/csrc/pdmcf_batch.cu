@@ -515,6 +515,12 @@ extern "C" int mcf_solve_batch(mcf_problem** probs, int count, const mcf_options
     return MCF_ERR_INVALID;
   }
   if (count == 0) return MCF_OK;
+  for (int i = 0; i < count; ++i)
+    if (probs[i] && probs[i]->busy.load() > 0) {
+      set_error("a problem in the batch has an outstanding ticket (collect it with mcf_poll or "
+                "mcf_wait, or discard it with mcf_cancel)");
+      return MCF_ERR_BUSY;
+    }
   const auto t0 = std::chrono::steady_clock::now();
   BatchEngine eng(opts->device, count);
   rc = eng.init();

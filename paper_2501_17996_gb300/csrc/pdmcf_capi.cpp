@@ -24,6 +24,11 @@ static thread_local std::string g_last_error;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+// A ticket of the problem has not been collected yet (see mcf_submit).
+static const char* const kOutstanding =
+    "the problem has an outstanding ticket (collect it with mcf_poll or mcf_wait, or discard "
+    "it with mcf_cancel)";
+
 static int fail(int code, const std::string& msg) {
   set_error(msg);
   return code;
@@ -294,6 +299,7 @@ int mcf_create_problem(int32_t n, int32_t m, const int32_t* tail, const int32_t*
 
 int mcf_update_capacities(mcf_problem* p, const double* cap) {
   if (!p) return fail(MCF_ERR_INVALID, "problem is NULL");
+  if (p->busy.load() > 0) return fail(MCF_ERR_BUSY, kOutstanding);
   int rc = check_caps(p->m, cap);
   if (rc != MCF_OK) return rc;
   std::lock_guard<std::mutex> g(p->lock);
@@ -304,6 +310,7 @@ int mcf_update_capacities(mcf_problem* p, const double* cap) {
 
 int mcf_update_weights(mcf_problem* p, const double* w) {
   if (!p) return fail(MCF_ERR_INVALID, "problem is NULL");
+  if (p->busy.load() > 0) return fail(MCF_ERR_BUSY, kOutstanding);
   int rc = check_weights(p->n, w);
   if (rc != MCF_OK) return rc;
   std::lock_guard<std::mutex> g(p->lock);
@@ -314,7 +321,7 @@ int mcf_update_weights(mcf_problem* p, const double* w) {
 
 int mcf_destroy_problem(mcf_problem* p) {
   if (!p) return MCF_OK;
-  if (p->busy.load() > 0) return fail(MCF_ERR_BUSY, "problem has a pending ticket");
+  if (p->busy.load() > 0) return fail(MCF_ERR_BUSY, kOutstanding);
   {
     std::lock_guard<std::mutex> g(p->lock);
     device_free(p);
@@ -345,6 +352,7 @@ int64_t mcf_problem_device_bytes(const mcf_problem* p, int precision) {
 static int solve_common(mcf_problem* p, const mcf_options* opts, mcf_result* res,
                         mcf_kernel_times* kt) {
   if (!p || !res) return fail(MCF_ERR_INVALID, "problem or result is NULL");
+  if (p->busy.load() > 0) return fail(MCF_ERR_BUSY, kOutstanding);
   int rc = validate_options(opts);
   if (rc != MCF_OK) return rc;
   const auto t0 = std::chrono::steady_clock::now();
@@ -357,6 +365,7 @@ static int solve_common(mcf_problem* p, const mcf_options* opts, mcf_result* res
 
 int mcf_autotune(mcf_problem* p, const mcf_options* opts, int* best_shape, double* ms_per_iter) {
   if (!p || !best_shape) return fail(MCF_ERR_INVALID, "problem or best_shape is NULL");
+  if (p->busy.load() > 0) return fail(MCF_ERR_BUSY, kOutstanding);
   int rc = validate_options(opts);
   if (rc != MCF_OK) return rc;
   std::lock_guard<std::mutex> g(p->lock);

@@ -1,12 +1,14 @@
 // pdmcf_noalloc.cu — mcf_project_capped_simplex_noalloc: the projection entry point for
 // callers that must not allocate device memory.
 //
-// Some callers cannot call cudaMalloc (or let a library call it for them): code that runs
-// while a CUDA graph is being captured, processes whose device memory is handed out by their
-// own pool or by a framework allocator, and real-time loops that must not enter the
-// allocator. This variant runs the same projection kernel as mcf_project_capped_simplex, but
-// its scratch (one double per column plus one for the total) lives in the fixed array below,
-// which every GPU that loads this library holds until the process exits.
+// Some callers cannot call cudaMalloc (or let a library call it for them): processes whose
+// device memory is handed out by their own pool or by a framework allocator that must see
+// every allocation, and real-time loops that must not enter the allocator (a cudaMalloc can
+// synchronize the device and take milliseconds). This variant runs the same projection
+// kernel as mcf_project_capped_simplex, but its scratch (one double per column plus one for
+// the total) lives in the fixed array below, which every GPU that loads this library holds
+// until the process exits.
+#include <cuda.h>   // CUcontext and CUresult only: the two driver calls come through cudart
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -32,11 +34,45 @@ static __device__ __align__(256) double g_noalloc_scratch[MCF_NOALLOC_MAX_COLS +
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-double* g_scratch_addr[kMaxDevices] = {};
+struct ScratchAddr {
+  unsigned long long ctx_id = 0;   // context the address belongs to (0: not looked up)
+  double* addr = nullptr;
+};
+ScratchAddr g_scratch[kMaxDevices];
 
-// Device address of the scratch array on the current device, looked up once per device
-// (with that device current). In host code the array's name is only a host-side stand-in,
-// so kernels must be given this address instead.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Unique id of the calling thread's current context (0 if none or not available). The
+// driver functions are reached through cudart, so the library needs no link to libcuda.
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(fn);
+    fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(fn);
+  });
+  if (!get_current || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+  if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
+
+// Device address of the scratch array in the current device's context. In host code the
+// array's name is only a host-side stand-in, so kernels must be given this address. It is
+// looked up with the device current on the first call per device, and again whenever the
+// context has changed since (a cudaDeviceReset by the application destroys the context that
+// held the old address).
 int scratch_address(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -49,7 +85,9 @@ int scratch_address(double** out) {
     return MCF_ERR_INVALID;
   }
   std::lock_guard<std::mutex> g(g_mu);
-  if (!g_scratch_addr[dev]) {
+  ScratchAddr& s = g_scratch[dev];
+  const unsigned long long ctx = current_context_id();
+  if (!s.addr || ctx == 0 || ctx != s.ctx_id) {
     double* p = nullptr;
     e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
     if (e != cudaSuccess || p == nullptr) {
@@ -57,9 +95,10 @@ int scratch_address(double** out) {
                        cudaGetErrorString(e));
       return MCF_ERR_CUDA;
     }
-    g_scratch_addr[dev] = p;
+    s.addr = p;
+    s.ctx_id = current_context_id();   // the lookup makes the primary context current
   }
-  *out = g_scratch_addr[dev];
+  *out = s.addr;
   return MCF_OK;
 }
 }  // namespace

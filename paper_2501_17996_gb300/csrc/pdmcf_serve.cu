@@ -10,6 +10,12 @@
 // (F, Y, omega) resident after a solve, so a request with warm_start = 1 re-solves from it
 // (Sec. 3.1, warm start). Requests the batched kernels do not serve (FP64 or BF16 storage,
 // a forced launch shape) run one at a time on a helper thread.
+//
+// A problem has at most one outstanding ticket: from mcf_submit until the ticket is
+// collected (the poll or wait that reports its final status, or mcf_cancel of a finished
+// ticket). A finished ticket's T, F and Y are read from the problem's device state when it is
+// collected, so no other solve may touch that state in between; the same rule means the
+// scheduler never holds the problem lock of one ticket while trying to take it for another.
 #include <stdint.h>
 
 #include <chrono>
@@ -52,16 +58,7 @@ bool batchable(const mcf_problem* p, const mcf_options& o) {
 
 class Server {
  public:
-  ~Server() {
-    {
-      std::lock_guard<std::mutex> g(mu_);
-      stop_ = true;
-    }
-    cv_work_.notify_all();
-    cv_solo_.notify_all();
-    if (sched_.joinable()) sched_.join();
-    if (solo_.joinable()) solo_.join();
-  }
+  ~Server() { shutdown(false); }
 
   int submit(mcf_problem* p, const mcf_options* o, mcf_ticket* out) {
     const bool batch = batchable(p, *o);
@@ -76,6 +73,12 @@ class Server {
       set_error("submission queue is full");
       return MCF_ERR_BUSY;
     }
+    int idle = 0;
+    if (!p->busy.compare_exchange_strong(idle, 1)) {
+      set_error("the problem has an outstanding ticket: collect it with mcf_poll or mcf_wait, "
+                "or discard it with mcf_cancel, before submitting another");
+      return MCF_ERR_BUSY;
+    }
     auto t = std::make_shared<Ticket>();
     t->id = next_id_++;
     t->p = p;
@@ -83,7 +86,6 @@ class Server {
     t->bytes = bytes;
     t->solo = !batch;
     t->t_submit = std::chrono::steady_clock::now();
-    p->busy.fetch_add(1);
     tickets_[t->id] = t;
     if (t->solo) {
       solo_queue_.push_back(t);
@@ -119,6 +121,7 @@ class Server {
     if (t->status == MCF_PENDING) return MCF_PENDING;
     tickets_.erase(id);
     g.unlock();
+    int rc = MCF_OK;
     if (res) {
       double *T = res->T, *F = res->F, *Y = res->Y;
       *res = t->res;
@@ -128,11 +131,11 @@ class Server {
       res->status = t->status;
       if ((T || F || Y) && (t->status == MCF_OK || t->status == MCF_ERR_NOT_CONVERGED)) {
         std::lock_guard<std::mutex> pg(t->p->lock);
-        int rc = device_copy_outputs(t->p, res);
-        if (rc != MCF_OK) return rc;
+        rc = device_copy_outputs(t->p, res);
       }
     }
-    return MCF_OK;
+    t->p->busy.store(0);   // collected: the problem takes new work again
+    return rc;
   }
 
   int cancel(mcf_ticket id) {
@@ -143,29 +146,60 @@ class Server {
       return MCF_ERR_INVALID;
     }
     std::shared_ptr<Ticket> t = it->second;
-    if (t->status != MCF_PENDING) return MCF_OK;
+    if (t->status != MCF_PENDING) {   // finished and not collected: discard the result
+      tickets_.erase(it);
+      t->p->busy.store(0);
+      return MCF_OK;
+    }
     t->cancelled = true;
     if (!t->started) {
       auto& q = t->solo ? solo_queue_ : queue_;
       for (auto qi = q.begin(); qi != q.end(); ++qi)
         if ((*qi)->id == id) { q.erase(qi); break; }
-      t->status = MCF_ERR_CANCELLED;
-      t->p->busy.fetch_sub(1);
-      cv_done_.notify_all();
+      finish_unstarted(t);
     }
+    // a started batched ticket leaves its slot at the next chunk boundary (schedule_loop);
+    // a started one-at-a-time ticket runs to its stop rule and then reports the cancellation
     return MCF_OK;
   }
 
   int config(int64_t budget, int max_resident) {
-    if (budget <= 0 || max_resident <= 0) {
-      set_error("budget and max_resident must be > 0");
+    if (budget <= 0 || max_resident < 0) {
+      set_error("budget must be > 0 and max_resident >= 0");
       return MCF_ERR_INVALID;
     }
     std::lock_guard<std::mutex> g(mu_);
     budget_ = budget;
     max_resident_ = max_resident;
     cv_work_.notify_all();
+    cv_solo_.notify_all();
     return MCF_OK;
+  }
+
+  // Stop both threads. Every ticket not finished yet ends with MCF_ERR_CANCELLED: queued
+  // ones at once, running batched ones after the chunk in progress (their slots are
+  // released, leaving the problem's iterate where the chunk ended, when release_state),
+  // a running one-at-a-time solve when it returns. A later mcf_submit starts the threads
+  // again. At process exit (release_state false) no CUDA call is made: the engines are
+  // left to the driver's teardown.
+  void shutdown(bool release_state) {
+    {
+      std::lock_guard<std::mutex> g(mu_);
+      stop_ = true;
+      release_state_ = release_state;
+    }
+    cv_work_.notify_all();
+    cv_solo_.notify_all();
+    if (sched_.joinable()) sched_.join();
+    if (solo_.joinable()) solo_.join();
+    std::lock_guard<std::mutex> g(mu_);
+    if (release_state) {
+      engines_.clear();
+    } else {
+      for (auto& kv : engines_) (void)kv.second.release();
+      engines_.clear();
+    }
+    stop_ = false;
   }
 
  private:
@@ -186,7 +220,12 @@ class Server {
       if (resident_ >= max_resident_) break;
       if (in_use_ + t->bytes > budget_) { ++qi; continue; }
       BatchEngine* eng = engine_for(t->opts.device);
-      if (!eng || eng->free_slots() == 0) { ++qi; continue; }
+      if (!eng) {   // no usable device: the request cannot run
+        qi = queue_.erase(qi);
+        finish_unstarted(t, MCF_ERR_CUDA);
+        continue;
+      }
+      if (eng->free_slots() == 0) { ++qi; continue; }
       if (!t->p->lock.try_lock()) { ++qi; continue; }   // a synchronous call holds it
       qi = queue_.erase(qi);
       t->started = true;
@@ -216,19 +255,65 @@ class Server {
     t->status = t->cancelled ? MCF_ERR_CANCELLED : rc;
     t->res.status = t->status;
     t->res.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t->t_submit).count();
-    t->p->busy.fetch_sub(1);
     cv_done_.notify_all();
+  }
+
+  void finish_unstarted(const std::shared_ptr<Ticket>& t, int rc = MCF_ERR_CANCELLED) {
+    // mu_ held; the ticket was never admitted
+    t->status = rc;
+    t->res.status = rc;
+    t->res.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t->t_submit).count();
+    cv_done_.notify_all();
+  }
+
+  // Release the engine slots of these running tickets (no lock held: the engines belong to
+  // the scheduler thread), then, with mu_ held, unlock their problems and finish them.
+  void retire(std::unique_lock<std::mutex>& g, std::vector<std::shared_ptr<Ticket>>& ts, int rc,
+              bool release) {
+    for (auto& t : ts) running_.erase(t.get());
+    g.unlock();
+    if (release)
+      for (auto& t : ts) {
+        auto it = engines_.find(t->opts.device);
+        if (it != engines_.end() && t->slot >= 0) it->second->release(t->slot);
+      }
+    g.lock();
+    for (auto& t : ts) {
+      t->p->lock.unlock();
+      finish(t, rc);
+    }
+    ts.clear();
   }
 
   void schedule_loop() {
     std::unique_lock<std::mutex> g(mu_);
     for (;;) {
+      if (stop_) {   // shutdown: cancel what runs and what waits
+        std::vector<std::shared_ptr<Ticket>> all;
+        for (auto& kv : running_) {
+          kv.second->cancelled = true;
+          all.push_back(kv.second);
+        }
+        retire(g, all, MCF_ERR_CANCELLED, release_state_);
+        for (auto& t : queue_) finish_unstarted(t);
+        queue_.clear();
+        return;
+      }
       admit(g);
-      const bool any = !running_.empty();
-      if (!any) {
-        if (stop_) return;
-        cv_work_.wait(g, [&] { return stop_ || !queue_.empty(); });
-        if (stop_ && queue_.empty()) return;
+      if (running_.empty()) {
+        const bool paused = max_resident_ == 0;
+        if (queue_.empty() || paused)
+          cv_work_.wait(g, [&] { return stop_ || (!queue_.empty() && max_resident_ > 0); });
+        else   // queued work whose problem a synchronous call still holds
+          cv_work_.wait_for(g, std::chrono::milliseconds(2));
+        continue;
+      }
+      // running tickets cancelled since the last chunk leave their slots now
+      std::vector<std::shared_ptr<Ticket>> gone;
+      for (auto& kv : running_)
+        if (kv.second->cancelled) gone.push_back(kv.second);
+      if (!gone.empty()) {
+        retire(g, gone, MCF_ERR_CANCELLED, true);
         continue;
       }
       g.unlock();
@@ -258,11 +343,13 @@ class Server {
         finish(t, dn.second.status);
       }
       if (err != MCF_OK) {   // a device error ends every running request
-        for (auto& kv : running_) {
-          kv.second->p->lock.unlock();
-          finish(kv.second, err);
-        }
-        running_.clear();
+        std::vector<std::shared_ptr<Ticket>> all;
+        for (auto& kv : running_) all.push_back(kv.second);
+        retire(g, all, err, true);
+        // rebuild the engines on the next admission rather than reuse a failed one
+        g.unlock();
+        engines_.clear();
+        g.lock();
       }
     }
   }
@@ -270,8 +357,12 @@ class Server {
   void solo_loop() {
     std::unique_lock<std::mutex> g(mu_);
     for (;;) {
-      cv_solo_.wait(g, [&] { return stop_ || !solo_queue_.empty(); });
-      if (stop_) return;
+      cv_solo_.wait(g, [&] { return stop_ || (!solo_queue_.empty() && max_resident_ > 0); });
+      if (stop_) {
+        for (auto& t : solo_queue_) finish_unstarted(t);
+        solo_queue_.clear();
+        return;
+      }
       std::shared_ptr<Ticket> t = solo_queue_.front();
       solo_queue_.pop_front();
       t->started = true;
@@ -305,6 +396,7 @@ class Server {
   int resident_ = 0;
   int max_queue_ = 1 << 16;
   bool stop_ = false;
+  bool release_state_ = true;
 };
 
 Server& server() {
@@ -341,6 +433,11 @@ int mcf_cancel(mcf_ticket ticket) { return server().cancel(ticket); }
 
 int mcf_serving_config(int64_t hbm_budget_bytes, int max_resident) {
   return server().config(hbm_budget_bytes, max_resident);
+}
+
+int mcf_serving_shutdown(void) {
+  server().shutdown(true);
+  return MCF_OK;
 }
 
 }  // extern "C"

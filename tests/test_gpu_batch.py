@@ -147,3 +147,65 @@ def test_batch_autotuned_classes_keep_alone_equal_in_mix(lib):
         assert np.abs(a["T"][m] - b["T"][m]).max() <= 1e-4 * np.abs(b["T"][m]).max()
     for p in probs:
         p.close()
+
+
+def test_served_ticket_outputs_are_its_own(lib):
+    """A finished ticket's T is read when it is collected; a second submission on the same
+    problem is refused until then, so back-to-back requests each return their own solve."""
+    inst = I.batched(seed=5, count=1)[0]
+    opts = dict(stop_mode="none", k_check=50)
+    with lib.Problem(inst) as p:
+        _, (ref100,) = lib.mcf_solve_batch([p], lib.mcf_options_default(max_iters=100, **opts),
+                                           want_T=True)
+        _, (ref300,) = lib.mcf_solve_batch([p], lib.mcf_options_default(max_iters=300, **opts),
+                                           want_T=True)
+        t1 = p.submit(max_iters=100, **opts)
+        with pytest.raises(lib.MCFError) as ei:
+            p.submit(max_iters=300, **opts)
+        assert ei.value.code == lib.MCF_ERR_BUSY
+        r1 = lib.mcf_wait(t1, 120000, p.n, p.m, want_T=True)
+        t2 = p.submit(max_iters=300, **opts)
+        r2 = lib.mcf_wait(t2, 120000, p.n, p.m, want_T=True)
+        assert r1["iters"] == 100 and r2["iters"] == 300
+        m = off(inst.n)
+        scale = np.abs(ref300["T"][m]).max()
+        assert np.abs(ref300["T"][m] - ref100["T"][m]).max() > 1e-3 * scale   # distinct results
+        assert np.abs(r1["T"][m] - ref100["T"][m]).max() <= 1e-6 * scale
+        assert np.abs(r2["T"][m] - ref300["T"][m]).max() <= 1e-6 * scale
+
+
+def test_served_cancel_stops_a_running_ticket(lib):
+    """mcf_cancel on a started batched ticket releases its slot at the next chunk boundary
+    instead of letting it run to max_iters; the problem then takes new work."""
+    import time
+
+    inst = I.served_network(1000, seed=1)
+    with lib.Problem(inst) as p:
+        t = p.submit(stop_mode="none", max_iters=10**7, k_check=50)
+        time.sleep(0.5)
+        lib.mcf_cancel(t)
+        r = lib.mcf_wait(t, 30000)
+        assert r is not None, "a cancelled running ticket did not finish"
+        assert r["status"] == lib.MCF_ERR_CANCELLED
+        t2 = p.submit(stop_mode="none", max_iters=20, k_check=10)
+        r2 = lib.mcf_wait(t2, 60000)
+        assert r2["status"] == lib.MCF_OK and r2["iters"] == 20
+
+
+def test_serving_shutdown_with_running_and_queued_tickets(lib):
+    """Shutdown ends every unfinished ticket with MCF_ERR_CANCELLED (running ones after the
+    chunk in progress) and the scheduler restarts on the next submission."""
+    insts = I.batched(seed=13, count=4)
+    probs = [lib.Problem(i) for i in insts]
+    tickets = [p.submit(stop_mode="none", max_iters=10**7, k_check=50) for p in probs]
+    import time
+
+    time.sleep(0.3)
+    lib.mcf_serving_shutdown()
+    for t in tickets:
+        r = lib.mcf_wait(t, 30000)
+        assert r is not None and r["status"] == lib.MCF_ERR_CANCELLED
+    t = probs[0].submit(stop_mode="none", max_iters=20, k_check=10)
+    assert lib.mcf_wait(t, 60000)["status"] == lib.MCF_OK
+    for p in probs:
+        p.close()
