@@ -327,6 +327,17 @@ int mcf_autotune(mcf_problem* p, const mcf_options* opts, int* best_shape, doubl
  * fills the four arrays (each may be NULL) up to that count. */
 int mcf_shape_info(int* group, int* vpt, int* block, int* kind);
 
+/* ---------------------------------------------------------------- testing aids */
+
+/* Exercise the bounded device-side waits: the next solve whose edge phase is the bulk-copy
+ * pipelined kind (mcf_shape_info kind 1) arms the first shared-memory stage of its block 0
+ * for copies that it never issues, in its first iteration. That stage's mbarrier wait then
+ * gives up (2^22 polls or 2 s), the block drains its own copies (bounded the same way) and
+ * returns, and the solve ends with MCF_ERR_CUDA ("a bounded device-side wait timed out");
+ * no copy is left in flight and the context stays usable. The problem's iterate is then
+ * invalid, so the next solve starts cold. The paper has no counterpart. Returns MCF_OK. */
+int mcf_test_withhold_next_copy(void);
+
 /* Message for the last error of the calling thread ("" if none). */
 const char* mcf_last_error(void);
 

@@ -73,7 +73,7 @@ SYMBOLS = [
     "mcf_options_default", "mcf_solve", "mcf_solve_timed", "mcf_solve_batch", "mcf_autotune",
     "mcf_submit", "mcf_poll", "mcf_wait",
     "mcf_cancel", "mcf_serving_config", "mcf_serving_shutdown", "mcf_project_capped_simplex",
-    "mcf_project_capped_simplex_noalloc", "mcf_shape_info",
+    "mcf_project_capped_simplex_noalloc", "mcf_shape_info", "mcf_test_withhold_next_copy",
     "mcf_last_error", "mcf_version",
 ]
 
@@ -110,6 +110,7 @@ def _load() -> C.CDLL:
         "mcf_cancel": (C.c_int, [C.c_int64]),
         "mcf_serving_config": (C.c_int, [C.c_int64, C.c_int]),
         "mcf_serving_shutdown": (C.c_int, []),
+        "mcf_test_withhold_next_copy": (C.c_int, []),
         "mcf_project_capped_simplex": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P, P, P,
                                                  dp, P]),
         "mcf_project_capped_simplex_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P, P,
@@ -364,6 +365,14 @@ def mcf_serving_config(hbm_budget_bytes: int, max_resident: int) -> None:
     rc = LIB.mcf_serving_config(int(hbm_budget_bytes), int(max_resident))
     if rc != MCF_OK:
         raise MCFError(rc, "mcf_serving_config")
+
+
+def mcf_test_withhold_next_copy() -> None:
+    """Testing aid: the next bulk-copy pipelined solve has one stage whose copies never come,
+    so its bounded device wait runs out (see the header)."""
+    rc = LIB.mcf_test_withhold_next_copy()
+    if rc != MCF_OK:
+        raise MCFError(rc, "mcf_test_withhold_next_copy")
 
 
 def mcf_serving_shutdown() -> None:

@@ -184,6 +184,10 @@ template <int GROUP> struct GroupScratch {
   double x[2][NW];
   float sf[2][NW];   // FP32 partials stay FP32: a double round trip would run on the FP64 pipe
   float xf[2][NW];
+  float mnf[2][NW];  // per-warp minima / maxima of the projection's certificates
+  float mxf[2][NW];
+  double mnd[2][NW];
+  double mxd[2][NW];
 };
 
 // Cross-warp stage of a block-wide group reduction: lane l < NW of every warp loads warp
@@ -221,6 +225,76 @@ __device__ __forceinline__ void group_sum_count(P& s, int& c, GroupScratch<GROUP
     int pc = lane < NW ? sh.c[phase][lane] : 0;
     s = cross_warp<NW>(ps, P(0), [](P a, P b) { return a + b; });
     c = cross_warp<NW>(pc, 0, [](int a, int b) { return a + b; });
+    phase ^= 1;
+  }
+}
+
+// Warp-wide minimum / maximum, the same value in every lane: one redux instruction for
+// FP32, a butterfly for FP64.
+__device__ __forceinline__ float warp_min(float v) {
+  float r;
+  asm("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+  return r;
+}
+__device__ __forceinline__ float warp_max(float v) {
+  float r;
+  asm("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+  return r;
+}
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Group-wide statistics of one projection pass: the sum and count of the active entries
+// (the same butterfly as group_sum_count, so the sum is bitwise the same), the smallest
+// active entry and, with IMAX, the largest inactive one.
+template <int GROUP, bool IMAX, typename P>
+__device__ __forceinline__ void group_stats(P& s, int& c, P& amin, P& imax,
+                                            GroupScratch<GROUP>& sh, int& phase) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  c = __reduce_add_sync(0xffffffffu, c);
+  amin = warp_min(amin);
+  if constexpr (IMAX) imax = warp_max(imax);
+  if constexpr (GROUP > 32) {
+    constexpr int NW = GROUP / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    P ps, pmn, pmx = P(0);
+    if constexpr (std::is_same<P, float>::value) {
+      if (lane == 0) {
+        sh.sf[phase][warp] = s;
+        sh.c[phase][warp] = c;
+        sh.mnf[phase][warp] = amin;
+        if constexpr (IMAX) sh.mxf[phase][warp] = imax;
+      }
+      __syncthreads();
+      ps = lane < NW ? sh.sf[phase][lane] : 0.f;
+      pmn = lane < NW ? sh.mnf[phase][lane] : INFINITY;
+      if constexpr (IMAX) pmx = lane < NW ? sh.mxf[phase][lane] : -INFINITY;
+    } else {
+      if (lane == 0) {
+        sh.s[phase][warp] = (double)s;
+        sh.c[phase][warp] = c;
+        sh.mnd[phase][warp] = (double)amin;
+        if constexpr (IMAX) sh.mxd[phase][warp] = (double)imax;
+      }
+      __syncthreads();
+      ps = lane < NW ? (P)sh.s[phase][lane] : P(0);
+      pmn = lane < NW ? (P)sh.mnd[phase][lane] : (P)INFINITY;
+      if constexpr (IMAX) pmx = lane < NW ? (P)sh.mxd[phase][lane] : (P)(-INFINITY);
+    }
+    const int pc = lane < NW ? sh.c[phase][lane] : 0;
+    s = cross_warp<NW>(ps, P(0), [](P a, P b) { return a + b; });
+    c = __reduce_add_sync(0xffffffffu, pc);
+    amin = warp_min(pmn);
+    if constexpr (IMAX) imax = warp_max(pmx);
     phase ^= 1;
   }
 }
@@ -547,6 +621,8 @@ struct IterArgs {
   P rho;
   int parity;         // F[parity], Y[parity] hold F^{k-1/2}, Y^k; the other slot receives k+1
   int check;          // 1 on check iterations
+  int withhold;       // testing aid (bulk-copy edge phase): block 0 arms its first stage for
+                      // copies it never issues, so that stage's bounded wait runs out
 };
 
 // ------------------------------------------------------------------ projection
@@ -581,6 +657,32 @@ __device__ __forceinline__ void shifted_mu(P m0, P m0l, P nu, P& hi, P& lo) {
   lo = l - (hi - s);
 }
 
+// ------------------------------------------------------------------ packed FP32 pairs
+// sm_100-class SMs issue two FP32 adds, multiplies or FMAs as one instruction
+// (add/sub/mul/fma.rn.f32x2); each lane is rounded exactly like the scalar operation, so the
+// packed code gives bitwise the scalar results with half the instructions.
+__device__ __forceinline__ float2 p2_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p2_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p2_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p2_sub(float2 a, float2 b) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 p2(float x) { return make_float2(x, x); }
+
+// shifted_q on a pair of entries (the same operations in the same order, packed).
+__device__ __forceinline__ float2 shifted_q2(float2 f, float2 yh, float2 yt, float2 dl,
+                                             float2 alpha, float2 nm0, float2 nm0l) {
+  const float2 s = p2_sub(yh, yt);
+  const float2 bb = p2_sub(s, yh);
+  const float2 err = p2_sub(p2_sub(yh, p2_sub(s, bb)), p2_add(yt, bb));
+  return p2_add(f, p2_add(p2_fma(alpha, s, nm0), p2_fma(alpha, p2_add(err, dl), nm0l)));
+}
+
 // Capped-simplex projection of one column (Sec. 2.3): mu = 0 if sum (q)_+ <= c, else the
 // root of phi(mu) = sum_i (q_i - mu)_+ - c. phi is convex, decreasing and piecewise
 // linear, so Newton from a point left of the root, mu' = (sum_{q>mu} q - c)/#{q > mu},
@@ -589,33 +691,49 @@ __device__ __forceinline__ void shifted_mu(P m0, P m0l, P nu, P& hi, P& lo) {
 // The previous iteration's mu is the starting point; if it lies right of the root, one
 // Newton step from there lands at or left of the root (tangents of a convex function lie
 // below it). `lo` is the floor of mu: 0 for q itself, -mu0 in the shifted frame above.
+//
+// Each pass also returns the smallest active entry (and, on the first pass, the largest
+// inactive one). A Newton step mu -> mu' keeps the active set exactly when no entry lies
+// between them: mu' < min{q > mu} going right, mu' >= max{q <= mu} going left. Then
+// phi(mu') = 0 and mu' is returned without a confirming pass; the value is bitwise the one
+// the confirming pass would have accepted (same active set, same fixed-order sum).
 template <int GROUP, int VPT, int VW, typename P>
 __device__ __forceinline__ P project_mu(const P (&q)[VPT][VW], P c, P mu0, P lo,
                                         GroupScratch<GROUP>& sh, int& phase) {
-  auto eval = [&](P mu, P& s, int& cnt) {
-    P ls = 0; int lc = 0;
+  auto eval = [&](P mu, P& s, int& cnt, P& amin, P& imax, auto want_imax) {
+    constexpr bool IM = decltype(want_imax)::value;
+    P ls = 0, am = (P)INFINITY, im = (P)(-INFINITY);
+    int lc = 0;
 #pragma unroll
     for (int v = 0; v < VPT; ++v)
 #pragma unroll
-      for (int u = 0; u < VW; ++u)
-        if (q[v][u] > mu) { ls += q[v][u]; ++lc; }
-    group_sum_count<GROUP>(ls, lc, sh, phase);
-    s = ls; cnt = lc;
+      for (int u = 0; u < VW; ++u) {
+        const P x = q[v][u];
+        if (x > mu) { ls += x; ++lc; am = fmin(am, x); }
+        else if constexpr (IM) { im = fmax(im, x); }
+      }
+    group_stats<GROUP, IM, P>(ls, lc, am, im, sh, phase);
+    s = ls; cnt = lc; amin = am;
+    if constexpr (IM) imax = im;
   };
+  using with_imax = std::true_type;
+  using without_imax = std::false_type;
   P mu = mu0 > lo ? mu0 : lo;
-  P s; int cnt;
-  eval(mu, s, cnt);
+  P s, amin, imax;
+  int cnt;
+  eval(mu, s, cnt, amin, imax, with_imax{});
   P phi = s - (P)cnt * mu - c;
   if (phi <= P(0)) {
     if (mu == lo || phi == P(0)) return mu;            // at the floor, or exactly at the root
     P mn = cnt > 0 ? (s - c) / (P)cnt : lo;            // Newton step from the right
     if (mn <= lo) {
       mu = lo;
-      eval(mu, s, cnt);
+      eval(mu, s, cnt, amin, imax, without_imax{});
       if (s - (P)cnt * lo - c <= P(0)) return lo;
     } else {
+      if (cnt > 0 && mn >= imax) return mn;            // no inactive entry joins: the root
       mu = mn;
-      eval(mu, s, cnt);
+      eval(mu, s, cnt, amin, imax, without_imax{});
     }
   }
 #pragma unroll 1
@@ -623,10 +741,9 @@ __device__ __forceinline__ P project_mu(const P (&q)[VPT][VW], P c, P mu0, P lo,
     if (cnt == 0) break;
     const P mn = (s - c) / (P)cnt;
     if (!(mn > mu)) break;
-    const int prev = cnt;
+    if (mn < amin) return mn;                          // no active entry leaves: the root
     mu = mn;
-    eval(mu, s, cnt);
-    if (cnt == prev) break;
+    eval(mu, s, cnt, amin, imax, without_imax{});
   }
   return mu;
 }
@@ -953,6 +1070,7 @@ edge_tma_kernel(IterArgs<float, S> a) {
   auto issue = [&](int i) {   // thread 0: bring edge e0+i into stage i&1
     const int e = e0 + i, st = i & 1;
     mbar_arrive_expect_tx(&full[st], frow + yrow);
+    if (a.withhold && blockIdx.x == 0 && i == 0) return;   // the copies never come
     tma_load_1d(sF[st], Fo + (size_t)e * a.ld, frow, &full[st]);
     tma_load_1d(sY[st], Y + (size_t)a.e_tail[e] * a.ld, yrow, &full[st]);
   };
@@ -1092,10 +1210,13 @@ edge_tma_kernel(IterArgs<float, S> a) {
 // CTAs per SM): Y_{:,head} and the running in-sum of F^{k+1/2} live in this thread's slices
 // of shared memory (each thread touches only its own chunk positions, so no barriers are
 // added), and the in-sum is written to Pin[head] when the head changes, so the node phase
-// gathers only out-edges.
+// gathers only out-edges. One thread prefetches the next edge's F row and Y_{:,tail} row
+// into L2 while this edge is projected, and the per-entry arithmetic runs on packed FP32
+// pairs (FP32 iterates only).
 template <typename P, typename S, int VPT, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 2)
 edge_insum_kernel(IterArgs<P, S> a) {
+  static_assert(std::is_same<P, float>::value, "in-sum edge phase: FP32 iterates");
   constexpr int VW = StoreTraits<S>::VW;
   extern __shared__ __align__(16) unsigned char dyn_is[];
   P* yh_s = reinterpret_cast<P*>(dyn_is);
@@ -1104,14 +1225,17 @@ edge_insum_kernel(IterArgs<P, S> a) {
   int phase = 0;
   const int tid = threadIdx.x;
   const int nchunks = a.ld / VW;
-  const P alpha = (P)a.sc->alpha;
-  const P rho = a.rho;
+  const float alpha_s = (float)a.sc->alpha;
+  const float2 alpha = p2(alpha_s);
+  const float2 rho = p2(a.rho);
   const S* __restrict__ Fo = a.F[a.parity];
   S* __restrict__ Fn = a.F[a.parity ^ 1];
   const P* __restrict__ Y = a.Y[a.parity];
   const __nv_bfloat16* __restrict__ ylo = a.Ylo[a.parity];
   const int e0 = a.cta_ptr[blockIdx.x], e1 = a.cta_ptr[blockIdx.x + 1];
-  P dsum = P(0);   // this thread's ||dF||^2 over its edges (FP64 across threads)
+  const uint32_t frow = (uint32_t)a.ld * (uint32_t)sizeof(S);   // multiples of 16 bytes
+  const uint32_t yrow = (uint32_t)a.ld * 4u;
+  float2 dsum = p2(0.f);   // this thread's sum of (f^ - f)^2 over its edges (x rho^2 at the end)
   int cur_h = -1;
   auto flush = [&](int hh) {
     P* pr = a.Pin + (size_t)hh * a.ld;
@@ -1139,6 +1263,11 @@ edge_insum_kernel(IterArgs<P, S> a) {
       nc = a.cap[e + 1];
       nmu = a.mu[e + 1];
       nmul = a.mu_lo[e + 1];
+      if (tid == 0) {   // the next edge's streamed rows, into L2 during this edge's projection
+        prefetch_l2(Fo + (size_t)(e + 1) * a.ld, frow);
+        prefetch_l2(Y + (size_t)nt * a.ld, yrow);
+        if (ylo) prefetch_l2(ylo + (size_t)nt * a.ld, yrow / 2);
+      }
     }
     if (h != cur_h) {   // new head group: flush, then stage Y_{:,h} (its tail stays in L1/L2)
       if (cur_h >= 0) flush(cur_h);
@@ -1158,31 +1287,32 @@ edge_insum_kernel(IterArgs<P, S> a) {
     }
     const S* fo = Fo + (size_t)e * a.ld;
     const P* yt = Y + (size_t)t * a.ld;
+    const float2 nm0 = p2(-mu0), nm0l = p2(-mu0l);
     P q[VPT][VW], f[VPT][VW];
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
       const int ci = v * BLOCK + tid;
       if (ci < nchunks) {
         S fs[VW];
-        P a1[VW], a2[VW], dl[VW];
+        P a1[VW], a2[VW], l1[VW], l2[VW];
         ld_stream<S, VW>(fo + ci * VW, fs);
         ld_plain<P, VW>(yh_s + ci * VW, a1);
         ld_keep<P, VW>(yt + ci * VW, a2);
+        if (ylo) {
+          ld_lo<VW>(ylo + (size_t)h * a.ld + ci * VW, l1);
+          ld_lo<VW>(ylo + (size_t)t * a.ld + ci * VW, l2);
+        } else {
 #pragma unroll
-        for (int u = 0; u < VW; ++u) dl[u] = P(0);
-        if constexpr (std::is_same<P, float>::value) {
-          if (ylo) {
-            float l1[VW], l2[VW];
-            ld_lo<VW>(ylo + (size_t)h * a.ld + ci * VW, l1);
-            ld_lo<VW>(ylo + (size_t)t * a.ld + ci * VW, l2);
-#pragma unroll
-            for (int u = 0; u < VW; ++u) dl[u] = l1[u] - l2[u];
-          }
+          for (int u = 0; u < VW; ++u) { l1[u] = 0.f; l2[u] = 0.f; }
         }
 #pragma unroll
-        for (int u = 0; u < VW; ++u) {
-          f[v][u] = to_p<P>(fs[u]);
-          q[v][u] = shifted_q<P>(f[v][u], a1[u], a2[u], dl[u], alpha, mu0, mu0l);
+        for (int u = 0; u < VW; u += 2) {
+          const float2 ff = make_float2(to_p<P>(fs[u]), to_p<P>(fs[u + 1]));
+          const float2 dl = p2_sub(make_float2(l1[u], l1[u + 1]), make_float2(l2[u], l2[u + 1]));
+          const float2 qq = shifted_q2(ff, make_float2(a1[u], a1[u + 1]),
+                                       make_float2(a2[u], a2[u + 1]), dl, alpha, nm0, nm0l);
+          f[v][u] = ff.x; f[v][u + 1] = ff.y;
+          q[v][u] = qq.x; q[v][u + 1] = qq.y;
         }
       } else {
 #pragma unroll
@@ -1190,7 +1320,7 @@ edge_insum_kernel(IterArgs<P, S> a) {
       }
     }
     const P mu = project_mu<BLOCK, VPT, VW, P>(q, c, P(0), shifted_floor<P>(mu0, mu0l), sh, phase);
-    P dloc = P(0);
+    const float2 nmu2 = p2(-mu);
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
       const int ci = v * BLOCK + tid;
@@ -1199,18 +1329,23 @@ edge_insum_kernel(IterArgs<P, S> a) {
         P acc[VW];
         ld_plain<P, VW>(sin_s + ci * VW, acc);
 #pragma unroll
-        for (int u = 0; u < VW; ++u) {
-          const P fh = q[v][u] > mu ? q[v][u] - mu : P(0);
-          out[u] = from_p<S, P>(rho * fh + (P(1) - rho) * f[v][u]);
-          acc[u] += to_p<P>(out[u]);
-          const P d = rho * (fh - f[v][u]);   // the step itself (see edge_kernel)
-          dloc = fma(d, d, dloc);
+        for (int u = 0; u < VW; u += 2) {
+          const float2 ff = make_float2(f[v][u], f[v][u + 1]);
+          const float2 t2 = p2_add(make_float2(q[v][u], q[v][u + 1]), nmu2);
+          const float2 fh = make_float2(fmaxf(t2.x, 0.f), fmaxf(t2.y, 0.f));   // (q - mu)_+
+          const float2 st = p2_sub(fh, ff);                                      // f^ - f
+          const float2 fnew = p2_fma(rho, st, ff);        // rho f^ + (1 - rho) f
+          dsum = p2_fma(st, st, dsum);
+          out[u] = from_p<S, P>(fnew.x);
+          out[u + 1] = from_p<S, P>(fnew.y);
+          const float2 sum = p2_add(make_float2(acc[u], acc[u + 1]),
+                                    make_float2(to_p<P>(out[u]), to_p<P>(out[u + 1])));
+          acc[u] = sum.x; acc[u + 1] = sum.y;
         }
         st_stream<S, VW>(Fn + (size_t)e * a.ld + ci * VW, out);
         st_plain<P, VW>(sin_s + ci * VW, acc);
       }
     }
-    dsum += dloc;
     if (tid == 0) {
       P hi, lo;
       shifted_mu<P>(mu0, mu0l, mu, hi, lo);
@@ -1219,7 +1354,9 @@ edge_insum_kernel(IterArgs<P, S> a) {
     }
   }
   if (cur_h >= 0) flush(cur_h);
-  double v1[1] = {(double)dsum};
+  // Delta_F uses the step rho (f^ - f) itself, not the rounded stored iterate (see edge_kernel)
+  const float r2 = a.rho * a.rho;
+  double v1[1] = {(double)(r2 * (dsum.x + dsum.y))};
   block_sum_write<BLOCK, 1>(v1, a.part_edge + blockIdx.x);
 }
 

@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <type_traits>
 #include <cmath>
@@ -652,6 +653,11 @@ struct PhaseRule {
   bool skip_outputs = false;
 };
 
+// mcf_test_withhold_next_copy: one pending request, taken by the next solve that runs the
+// bulk-copy edge phase.
+static std::atomic<int> g_withhold_request{0};
+static bool take_withhold_request() { return g_withhold_request.exchange(0) != 0; }
+
 template <typename P, typename S>
 static int solve_t(mcf_problem* p, DeviceState* d, const mcf_options* o, mcf_result* res,
                    cudaStream_t st, mcf_kernel_times* kt, const PhaseRule& rule = PhaseRule()) {
@@ -703,6 +709,11 @@ static int solve_t(mcf_problem* p, DeviceState* d, const mcf_options* o, mcf_res
   }
   d->lo_live = lo;
   const IterArgs<P, S> args = make_args<P, S>(d, p, o->rho, lo);
+  // testing aid (mcf_test_withhold_next_copy): the first edge launch of this solve withholds
+  // block 0's first bulk copies, so its bounded wait runs out and the solve reports it
+  const bool withhold = d->tma >= 0 && d->tma_kind == 1 && take_withhold_request();
+  IterArgs<P, S> args_w = args;
+  args_w.withhold = 1;
   const int64_t max_iters = o->max_iters;
   const int kc = std::max(1, o->k_check);
   bool use_graphs = o->use_graphs && !d->graphs_broken && kt == nullptr;
@@ -732,19 +743,21 @@ static int solve_t(mcf_problem* p, DeviceState* d, const mcf_options* o, mcf_res
   bool any = false;
   while (k < max_iters) {
     const int64_t chunk = std::min<int64_t>(kc - (k % kc), max_iters - k);
-    if (use_graphs && chunk == kc) {
+    const bool stall_first = withhold && k == 0;
+    if (use_graphs && chunk == kc && !stall_first) {
       if (!d->graph[parity] && !capture_chunk<P, S>(d, args, parity, kc, st, &d->graph[parity])) {
         d->graphs_broken = true;
         use_graphs = false;
       }
     }
-    if (use_graphs && chunk == kc) {
+    if (use_graphs && chunk == kc && !stall_first) {
       CK(cudaGraphLaunch(d->graph[parity], st));
       if (kc & 1) parity ^= 1;
     } else {
       for (int64_t i = 0; i < chunk; ++i) {
-        if (kt) CK((launch_iteration_timed<P, S>(d, args, parity, i == chunk - 1, st, pool)));
-        else CK((launch_iteration<P, S>(d, args, parity, i == chunk - 1, st)));
+        const IterArgs<P, S>& ai = (stall_first && i == 0) ? args_w : args;
+        if (kt) CK((launch_iteration_timed<P, S>(d, ai, parity, i == chunk - 1, st, pool)));
+        else CK((launch_iteration<P, S>(d, ai, parity, i == chunk - 1, st)));
         parity ^= 1;
       }
     }
@@ -845,6 +858,11 @@ static int copy_outputs_t(mcf_problem* p, DeviceState* d, mcf_result* res, cudaS
 }
 
 }  // namespace pdmcf
+
+extern "C" int mcf_test_withhold_next_copy(void) {
+  pdmcf::g_withhold_request.store(1);
+  return MCF_OK;
+}
 
 extern "C" int mcf_shape_info(int* group, int* vpt, int* block, int* kind) {
   using namespace pdmcf;
