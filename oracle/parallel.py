@@ -15,8 +15,10 @@ over worker processes that share F, Y and the scratch arrays through shared memo
 
 The per-entry arithmetic is the oracle's; only the order of the sums in F+ A^T and in the two
 norms differs (blocks, then their total), so the iterates agree with oracle.pdmcf to rounding.
-The stop test is not evaluated (stop mode "none"); this module exists to time the method on
-every core, the "PDMCF (CPU)" configuration of the paper's Tables 1-2.
+`ParallelPDMCF.step` has the signature of oracle.pdmcf's `step` argument, so
+oracle.pdmcf(..., step=pp.step) runs Algorithm 2.1 (stop test, primal weight rule and its
+adaptation stop, metrics) with the updates spread over the workers; `run` performs plain
+iterations for timing, the "PDMCF (CPU)" configuration of the paper's Tables 1-2.
 """
 from __future__ import annotations
 
@@ -63,7 +65,10 @@ def _edge_block(args):
     Y = _W["Y%d" % src]
     Fp = _W["Fplus"]
     Q = F[:, lo:hi] + alpha * (Y[:, head[lo:hi]] - Y[:, tail[lo:hi]])
-    Fhat, _ = O.project_capped_simplex(Q, cap[lo:hi])
+    Fhat, mu = O.project_capped_simplex(Q, cap[lo:hi])
+    _W["Q"][:, lo:hi] = Q
+    _W["Fhat"][:, lo:hi] = Fhat
+    _W["mu"][0, lo:hi] = mu
     Fp[:, lo:hi] = 2.0 * Fhat - F[:, lo:hi]
     Fn[:, lo:hi] = rho * Fhat + (1.0 - rho) * F[:, lo:hi]
     d = Fn[:, lo:hi] - F[:, lo:hi]
@@ -92,14 +97,17 @@ def _node_block(args):
         Yhat[off] = O.prox_log(V[off], beta, w)
     else:
         Yhat[off] = O.prox_pow(V[off], beta, w, util.gamma[lo:hi][off])
+    _W["Yhat"][lo:hi] = Yhat
     Yn[lo:hi] = rho * Yhat + (1.0 - rho) * Y[lo:hi]
     d = Yn[lo:hi] - Y[lo:hi]
     return float(np.sum(d * d))
 
 
 class ParallelPDMCF:
-    """Worker pool holding one instance; `run(iters)` performs PDMCF iterations from the
-    cold start (F = 0, Y = I - 1 1^T, omega = 1) and returns (F, Y, omega) afterwards."""
+    """Worker pool holding one instance. `step` is oracle.pdmcf's update step; `run(iters)`
+    performs PDMCF iterations from the cold start (F = 0, Y = I - 1 1^T, omega = 1) and
+    returns (F, Y, omega) afterwards. Arrays that `step` returns are views of shared memory,
+    valid until the next step or `close` (copy what must outlive them)."""
 
     def __init__(self, inst, workers: int | None = None, rho=1.9, theta=0.5, k_adapt=100,
                  tau=1e-5):
@@ -109,7 +117,9 @@ class ParallelPDMCF:
         self.rho, self.theta, self.k_adapt, self.tau = rho, theta, k_adapt, tau
         self.eta = O.eta_bound(self.n, inst.tail, inst.head)
         n, m = self.n, self.m
-        shapes = {"F0": (n, m), "F1": (n, m), "Fplus": (n, m), "Y0": (n, n), "Y1": (n, n)}
+        shapes = {"F0": (n, m), "F1": (n, m), "Fplus": (n, m), "Y0": (n, n), "Y1": (n, n),
+                  "Q": (n, m), "Fhat": (n, m), "mu": (1, m), "Yhat": (n, n)}
+        self.cur = 0
         self._shm = {}
         specs = {}
         for key, shape in shapes.items():
@@ -127,31 +137,45 @@ class ParallelPDMCF:
         self._eblocks = [(lo, min(m, lo + step_e)) for lo in range(0, m, step_e)]
         self._nblocks = [(lo, min(n, lo + step_n)) for lo in range(0, n, step_n)]
 
-    def run(self, iters: int):
+    def step(self, F, Y, alpha, beta, rho):
+        """One update of Algorithm 2.1 step 2 from (F, Y): returns
+        (Q, F^, mu, Y^, F_new, Y_new, Delta_F, Delta_Y) as oracle.pdmcf computes them."""
         a = self._arr
-        a["F0"][:] = 0.0
-        a["Y0"][:] = np.eye(self.n) - np.ones((self.n, self.n))
+        src = self.cur
+        if F is not a["F%d" % src]:
+            a["F%d" % src][:] = F
+        if Y is not a["Y%d" % src]:
+            a["Y%d" % src][:] = Y
+        dF2 = sum(self._pool.map(_edge_block, [(lo, hi, src, alpha, rho)
+                                               for lo, hi in self._eblocks]))
+        dY2 = sum(self._pool.map(_node_block, [(lo, hi, src, beta, rho)
+                                               for lo, hi in self._nblocks]))
+        self.cur = 1 - src
+        return (a["Q"], a["Fhat"], a["mu"][0].copy(), a["Yhat"], a["F%d" % (1 - src)],
+                a["Y%d" % (1 - src)], math.sqrt(dF2), math.sqrt(dY2))
+
+    def run(self, iters: int):
+        F = np.zeros((self.n, self.m))
+        Y = np.eye(self.n) - np.ones((self.n, self.n))
         omega = 1.0
-        src = 0
         for k in range(iters):
             alpha, beta = self.eta / omega, self.eta * omega
-            dF2 = sum(self._pool.map(_edge_block, [(lo, hi, src, alpha, self.rho)
-                                                   for lo, hi in self._eblocks]))
-            dY2 = sum(self._pool.map(_node_block, [(lo, hi, src, beta, self.rho)
-                                                   for lo, hi in self._nblocks]))
-            dF, dY = math.sqrt(dF2), math.sqrt(dY2)
+            _, _, _, _, F, Y, dF, dY = self.step(F, Y, alpha, beta, self.rho)
             if k % self.k_adapt == 0 and dF > self.tau and dY > self.tau:
                 omega = (dY / dF) ** self.theta * omega ** (1.0 - self.theta)
-            src ^= 1
-        return a["F%d" % src].copy(), a["Y%d" % src].copy(), omega
+        return F.copy(), Y.copy(), omega
 
     def close(self):
         if self._pool is not None:
             self._pool.close()
             self._pool.join()
             self._pool = None
+        self._arr = {}
         for shm in self._shm.values():
-            shm.close()
+            try:
+                shm.close()
+            except BufferError:   # a caller still holds a view; the mapping ends with it
+                pass
             shm.unlink()
         self._shm = {}
 

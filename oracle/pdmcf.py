@@ -305,7 +305,8 @@ class Result:
 def pdmcf(n, tail, head, cap, kind, w, gamma=None, *, eps=1e-6, stop_mode="kkt",
           max_iters=100000, rho=1.9, theta=0.5, k_adapt=100, tau=1e-5,
           omega_freeze_iter=-1, k_check=1, F0=None, Y0=None, omega0=1.0,
-          adapt_guard=10.0, adapt_guard_below=1e-2, history=False, on_check=None) -> Result:
+          adapt_guard=10.0, adapt_guard_below=1e-2, history=False, on_check=None,
+          step=None) -> Result:
     """Algorithm 2.1 (PDMCF), float64.
 
     stop_mode: "paper" stops when r^k < n m eps (Sec. 2.5), "kkt" when rel_kkt^k < eps,
@@ -324,6 +325,11 @@ def pdmcf(n, tail, head, cap, kind, w, gamma=None, *, eps=1e-6, stop_mode="kkt",
 
     on_check, if given, is called with the record of every stop test (the same dict that
     ``history`` collects); it observes the run and changes nothing in it.
+
+    step, if given, performs the updates of step 2 in place of the formulas below:
+    step(F, Y, alpha, beta, rho) -> (Q, F^, mu, Y^, F_new, Y_new, Delta_F, Delta_Y), the same
+    quantities (oracle.parallel spreads them over processes); the rest of the algorithm
+    (stop test, primal weight rule, metrics) is unchanged.
     """
     tail = np.asarray(tail, dtype=np.int64)
     head = np.asarray(head, dtype=np.int64)
@@ -360,15 +366,18 @@ def pdmcf(n, tail, head, cap, kind, w, gamma=None, *, eps=1e-6, stop_mode="kkt",
         alpha = eta / omega
         beta = eta * omega
         # 2. PDHG updates (Eq. e-pdhg-step)
-        Q = F + alpha * np.asarray(Y @ A)
-        Fhat, mu = project_capped_simplex(Q, c)
-        Fplus = 2.0 * Fhat - F
-        V = Y - beta * np.asarray(Fplus @ AT)
-        Yhat = util.prox(V, beta)
-        F_new = rho * Fhat + (1.0 - rho) * F
-        Y_new = rho * Yhat + (1.0 - rho) * Y
-        dF = float(np.sqrt(np.sum((F_new - F) ** 2)))
-        dY = float(np.sqrt(np.sum((Y_new - Y) ** 2)))
+        if step is None:
+            Q = F + alpha * np.asarray(Y @ A)
+            Fhat, mu = project_capped_simplex(Q, c)
+            Fplus = 2.0 * Fhat - F
+            V = Y - beta * np.asarray(Fplus @ AT)
+            Yhat = util.prox(V, beta)
+            F_new = rho * Fhat + (1.0 - rho) * F
+            Y_new = rho * Yhat + (1.0 - rho) * Y
+            dF = float(np.sqrt(np.sum((F_new - F) ** 2)))
+            dY = float(np.sqrt(np.sum((Y_new - Y) ** 2)))
+        else:
+            Q, Fhat, mu, Yhat, F_new, Y_new, dF, dY = step(F, Y, alpha, beta, rho)
         # 3. adaptive primal weight (Eq. e-primal_weight)
         if (k % k_adapt == 0 and dF > tau and dY > tau
                 and (omega_freeze_iter < 0 or k < omega_freeze_iter)):

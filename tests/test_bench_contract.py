@@ -78,3 +78,25 @@ def test_all_cores_oracle_matches_the_oracle():
         assert np.abs(F - ref.F).max() <= 1e-11 * np.abs(ref.F).max()
         assert np.abs(Y - ref.Y).max() <= 1e-11 * np.abs(ref.Y).max()
         assert abs(omega - ref.omega) <= 1e-11 * ref.omega
+
+
+def test_oracle_with_the_parallel_step_matches_the_oracle():
+    """oracle.pdmcf with oracle.parallel's step (the path make_golden.py uses for the large
+    slice) reproduces the plain oracle: same stop, same iterations, T and U to rounding."""
+    import numpy as np
+
+    from oracle import pdmcf as O
+    from oracle.parallel import ParallelPDMCF
+    from paper_2501_17996_gb300 import instances as I
+
+    inst = I.mid(0)
+    kw = dict(eps=1e-3, stop_mode="kkt", max_iters=5000, k_check=50)
+    ref = O.pdmcf(inst.n, inst.tail, inst.head, inst.cap, inst.kind, inst.w, inst.gamma, **kw)
+    with ParallelPDMCF(inst, workers=3) as pp:
+        r = O.pdmcf(inst.n, inst.tail, inst.head, inst.cap, inst.kind, inst.w, inst.gamma,
+                    step=pp.step, **kw)
+        T, U, iters, om = r.T.copy(), r.utility, r.iters, r.omega
+    assert iters == ref.iters and ref.status == "converged"
+    assert np.abs(T - ref.T).max() <= 1e-9 * np.abs(ref.T).max()
+    assert abs(U - ref.utility) <= 1e-11 * abs(ref.utility)
+    assert abs(om - ref.omega) <= 1e-9 * ref.omega

@@ -397,41 +397,71 @@ def test_ring_pin_detects_planted_mistakes(monkeypatch):
 
 def test_adaptation_stop_keeps_omega_constant():
     """Sec. 2.4: omega may stop adapting from some iteration on and stays constant after.
-    With the guard the stop comes after the first stop test, in the final phase (rel_kkt
-    has been below 1e-2), whose rel_kkt exceeds guard x the smallest one so far or whose
-    omega is more than a factor guard away from its value when that phase began; before it the run equals the unguarded one, after it
-    omega never changes while the unguarded run keeps adapting."""
+
+    The trigger iterations below were read by hand off the stored record of the run that
+    never stops adapting (tests/golden/adapt_history_mid_s0.json: omega and rel_kkt at every
+    stop test, k_check = 50), under the rule's reading (stop from the check where omega leaves
+    a factor g^2 of omega_ref, its value at the first finite measure; or, in the final phase
+    that begins at the first check with rel_kkt below adapt_guard_below, where omega leaves a
+    factor g of its value there or rel_kkt exceeds g x the smallest so far):
+      g = 1.05: omega_ref = 2.12601 (k = 250), band [1.92836, 2.34392]; omega = 1.84946 at
+                k = 450 leaves it -> stop at 450.
+      g = 1.5:  band (i) [0.94489, 4.7835] never left before 1050; the final phase begins at
+                k = 650 (rel_kkt 0.00819) with omega_arm = 1.89063, band [1.26042, 2.83595];
+                omega = 1.16422 at k = 1050 leaves it -> stop at 1050.
+      g = 2.5, adapt_guard_below = 1e-3: band (i) [0.34016, 13.2876]; the final phase begins
+                at k = 1400 (rel_kkt 8.60e-4), omega_arm = 0.89045, band [0.35618, 2.22613],
+                never left; the smallest rel_kkt is 9.2716e-5 at k = 1950 and rel_kkt =
+                2.9316e-4 > 2.5 x 9.2716e-5 = 2.3179e-4 at k = 2050 -> stop at 2050.
+    Before the stop the run equals the unstopped one; after it omega never changes."""
+    import json
+
     inst = I.mid(0)
-    kw = dict(stop_mode="none", max_iters=1500, k_check=50, history=True)
     args = (inst.n, inst.tail, inst.head, inst.cap, inst.kind, inst.w, inst.gamma)
+    kw = dict(stop_mode="none", max_iters=2200, k_check=50, history=True)
+    rec = json.load(open(os.path.join(GOLDEN, "adapt_history_mid_s0.json")))["rows"]
     free = O.pdmcf(*args, adapt_guard=0, **kw)
-    held = O.pdmcf(*args, adapt_guard=1.05, **kw)
     assert free.omega_frozen_at == -1
-    # the final phase begins at the first check with rel_kkt below 1e-2 (omega_arm = omega
-    # there); the stop follows the first later check whose measure is above 1.05 x the best
-    # before it or whose omega is more than a factor 1.05 away from omega_arm
-    # (omega_ref: omega at the first finite measure; the stop also follows a check whose
-    # omega is more than a factor 1.05^2 away from it)
-    best, ref, arm, trigger = math.inf, 0.0, 0.0, None
-    for h in free.history:
-        fin, w = math.isfinite(h["rel_kkt"]), h["omega"]
-        if trigger is None and ((ref > 0 and (w > 1.05 ** 2 * ref or w * 1.05 ** 2 < ref)) or
-                                (arm > 0 and ((fin and h["rel_kkt"] > 1.05 * best)
-                                              or w > 1.05 * arm or w * 1.05 < arm))):
-            trigger = h["k"]
-        if fin:
-            best = min(best, h["rel_kkt"])
-            if ref == 0:
-                ref = w
-            if arm == 0 and best < 1e-2:
-                arm = w
-    assert trigger is not None and held.omega_frozen_at == trigger
-    for a, b in zip(free.history, held.history):
-        if a["k"] <= trigger:
-            assert a["omega"] == b["omega"] and a["rel_kkt"] == b["rel_kkt"]
-        else:
-            assert b["omega"] == held.history[trigger // 50 - 1]["omega"]
-    assert free.omega != held.omega
+    for h, (k, w, r) in zip(free.history, rec):   # the record is this run's
+        assert h["k"] == k and h["omega"] == pytest.approx(w, rel=1e-12)
+        assert (r is None and not math.isfinite(h["rel_kkt"])) or h["rel_kkt"] == pytest.approx(r, rel=1e-9)
+    for guard, below, trigger in ((1.05, 1e-2, 450), (1.5, 1e-2, 1050), (2.5, 1e-3, 2050)):
+        held = O.pdmcf(*args, adapt_guard=guard, adapt_guard_below=below, **kw)
+        assert held.omega_frozen_at == trigger, (guard, held.omega_frozen_at)
+        w_frozen = next(h["omega"] for h in held.history if h["k"] == trigger)
+        for a, b in zip(free.history, held.history):
+            if a["k"] <= trigger:
+                assert a["omega"] == b["omega"] and a["rel_kkt"] == b["rel_kkt"]
+            else:
+                assert b["omega"] == w_frozen
+        assert free.omega != held.omega
+
+
+def test_golden_solutions_are_the_literal_algorithm():
+    """Every stored solution is that of Algorithm 2.1 with omega adapting throughout
+    (Eq. e-primal_weight, adapt_guard = 0): the acceptance references (stopped at relative
+    KKT 1e-4) come from runs on which the adaptation stop never fired, and a converged
+    reference on which it fired is reproduced exactly by the run without the stop (on mid_s0
+    the stop fired at k = 2610, after the last change of omega)."""
+    import glob
+
+    files = sorted(glob.glob(os.path.join(GOLDEN, "oracle_*.npz")))
+    assert files
+    fired = []
+    for f in files:
+        g = np.load(f)
+        assert "omega_frozen_at" in g, f
+        if "kkt1e-4" in f:
+            assert int(g["omega_frozen_at"]) == -1, f
+        elif int(g["omega_frozen_at"]) != -1:
+            fired.append(os.path.basename(f))
+    assert fired == ["oracle_mid_s0.npz"]
+    inst = I.mid(0)
+    g = np.load(os.path.join(GOLDEN, "oracle_mid_s0.npz"))
+    r = O.pdmcf(inst.n, inst.tail, inst.head, inst.cap, inst.kind, inst.w, inst.gamma,
+                eps=1e-9, stop_mode="kkt", max_iters=100000, k_check=10, adapt_guard=0)
+    assert r.omega_frozen_at == -1 and r.iters == int(g["iters"])
+    assert np.array_equal(r.T, g["T"]) and r.utility == float(g["utility"])
 
 
 def test_warm_start_continues_the_iteration():
