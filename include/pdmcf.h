@@ -108,6 +108,13 @@ typedef struct mcf_options {
                                 the solve. 0 = adapt throughout (default 10). The result
                                 reports the iteration in omega_frozen_at.                  */
   double  adapt_guard_below; /* start of the final phase for adapt_guard (default 1e-2)   */
+  const char* check_log;     /* path of a file to which mcf_solve and mcf_solve_timed append
+                                one JSON line per stop test (every k_check iterations): k,
+                                omega, r/(n m), rel_kkt and its three parts, U, D, the
+                                fraction of nonpositive off-diagonal T, whether omega still
+                                adapts, the precision (the convergence diagnostics of
+                                Sec. 3.1); NULL = none (default). Non-finite values are
+                                written as null. Not used by batched or served solves      */
 } mcf_options;
 
 /* ---------------------------------------------------------------- results */
@@ -318,7 +325,9 @@ int mcf_project_capped_simplex_noalloc(int32_t n, int32_t m, int32_t ld, const f
 int mcf_autotune(mcf_problem* p, const mcf_options* opts, int* best_shape, double* ms_per_iter);
 
 /* Launch shape table: shape s gives `group` threads per edge/node, each holding `vpt`
- * 16-byte chunks of the edge/node vector (capacity group*vpt chunks of 16 bytes of F).
+ * chunks of the edge/node vector: for kind 0 a chunk is 16 bytes of F (4 FP32, 2 FP64 or
+ * 8 BF16 entries), for kinds 1 and 2 it is 4 entries whatever the storage type; a shape
+ * covers a problem when group*vpt chunks hold n rounded up to 8 entries.
  * kind[s]: 0 register shapes (grid-stride over edges); 1 bulk-copy pipelined edge phase
  * (cp.async.bulk into two shared-memory stages, one CTA per SM over head-aligned edge
  * ranges); 2 register edge phase over head-aligned edge ranges with per-head in-sums in
@@ -326,6 +335,25 @@ int mcf_autotune(mcf_problem* p, const mcf_options* opts, int* best_shape, doubl
  * kind 2 is the automatic choice for rows of 8 KB or more. Returns the number of shapes;
  * fills the four arrays (each may be NULL) up to that count. */
 int mcf_shape_info(int* group, int* vpt, int* block, int* kind);
+
+/* ---------------------------------------------------------------- warm-state checkpoint */
+
+/* Write the problem's resident warm state (Sec. 3.1 warm start: F^{k-1/2}, Y^k with its
+ * compensated tail, the state F^{k-1/2} A^T of the relaxation identity, the projection
+ * multipliers and omega) to a host file, in the library's internal layout. The problem must
+ * have been solved (MCF_ERR_INVALID otherwise). Synchronizes the device. Errors:
+ * MCF_ERR_INVALID (no state, file not writable), MCF_ERR_BUSY (outstanding ticket),
+ * MCF_ERR_OOM, MCF_ERR_CUDA. */
+int mcf_save_state(mcf_problem* p, const char* path);
+
+/* Read a file written by mcf_save_state into the problem's device state on `device`
+ * (allocating it if needed), so that the next solve with warm_start = 1 continues from it:
+ * the result equals that of a warm solve of the problem the state was saved from, bit for
+ * bit. The network (n, m, edges) must be the one the state was saved from; capacities and
+ * weights are the problem's own. Errors: MCF_ERR_INVALID (unreadable or foreign file,
+ * different network), MCF_ERR_BUSY, MCF_ERR_OOM, MCF_ERR_CUDA. The paper has no
+ * counterpart for the file itself; it carries the warm start across processes. */
+int mcf_load_state(mcf_problem* p, const char* path, int device);
 
 /* ---------------------------------------------------------------- testing aids */
 

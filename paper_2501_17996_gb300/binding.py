@@ -43,7 +43,7 @@ class mcf_options(C.Structure):
         ("use_graphs", C.c_int), ("device", C.c_int), ("cuda_stream", C.c_void_p),
         ("omega0", C.c_double), ("stall_checks", C.c_int), ("compensated_duals", C.c_int),
         ("autotune", C.c_int), ("shape", C.c_int), ("adapt_guard", C.c_double),
-        ("adapt_guard_below", C.c_double),
+        ("adapt_guard_below", C.c_double), ("check_log", C.c_char_p),
     ]
 
 
@@ -74,6 +74,7 @@ SYMBOLS = [
     "mcf_submit", "mcf_poll", "mcf_wait",
     "mcf_cancel", "mcf_serving_config", "mcf_serving_shutdown", "mcf_project_capped_simplex",
     "mcf_project_capped_simplex_noalloc", "mcf_shape_info", "mcf_test_withhold_next_copy",
+    "mcf_save_state", "mcf_load_state",
     "mcf_last_error", "mcf_version",
 ]
 
@@ -111,6 +112,8 @@ def _load() -> C.CDLL:
         "mcf_serving_config": (C.c_int, [C.c_int64, C.c_int]),
         "mcf_serving_shutdown": (C.c_int, []),
         "mcf_test_withhold_next_copy": (C.c_int, []),
+        "mcf_save_state": (C.c_int, [P, C.c_char_p]),
+        "mcf_load_state": (C.c_int, [P, C.c_char_p, C.c_int]),
         "mcf_project_capped_simplex": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P, P, P,
                                                  dp, P]),
         "mcf_project_capped_simplex_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, P, P, P,
@@ -173,6 +176,8 @@ def mcf_options_default(**overrides) -> mcf_options:
             v = PRECISIONS[v]
         if k == "stop_mode" and isinstance(v, str):
             v = STOP_MODES[v]
+        if k == "check_log" and isinstance(v, str):
+            v = v.encode()
         setattr(o, k, v)
     return o
 
@@ -405,6 +410,16 @@ class Problem:
 
     def submit(self, **opts) -> int:
         return mcf_submit(self.h, mcf_options_default(**opts))
+
+    def save_state(self, path: str) -> None:
+        rc = LIB.mcf_save_state(self.h, os.fsencode(path))
+        if rc != MCF_OK:
+            raise MCFError(rc, "mcf_save_state")
+
+    def load_state(self, path: str, device: int = 0) -> None:
+        rc = LIB.mcf_load_state(self.h, os.fsencode(path), int(device))
+        if rc != MCF_OK:
+            raise MCFError(rc, "mcf_load_state")
 
     def update_capacities(self, cap):
         mcf_update_capacities(self.h, cap)

@@ -379,9 +379,10 @@ int mcf_autotune(mcf_problem* p, const mcf_options* opts, int* best_shape, doubl
       cap0 = group[s] * vpt[s];
   int best = -1;
   double best_ms = 1e300;
+  const int nchunks_rows = ((p->n + 7) / 8 * 8) / 4;   // kinds 1 and 2: 4-entry chunks
   for (int s = 0; s < count; ++s) {
     const int cap = group[s] * vpt[s];
-    if (cap < nchunks) continue;
+    if (cap < (pipelined[s] ? nchunks_rows : nchunks)) continue;
     if (pipelined[s] ? opts->precision == MCF_FP64 : cap > 4 * cap0) continue;
     mcf_options o = *opts;
     o.shape = s;
@@ -403,6 +404,20 @@ int mcf_autotune(mcf_problem* p, const mcf_options* opts, int* best_shape, doubl
   *best_shape = best;
   if (ms_per_iter) *ms_per_iter = best_ms;
   return MCF_OK;
+}
+
+int mcf_save_state(mcf_problem* p, const char* path) {
+  if (!p || !path) return fail(MCF_ERR_INVALID, "problem or path is NULL");
+  if (p->busy.load() > 0) return fail(MCF_ERR_BUSY, kOutstanding);
+  std::lock_guard<std::mutex> g(p->lock);
+  return device_save_state(p, path);
+}
+
+int mcf_load_state(mcf_problem* p, const char* path, int device) {
+  if (!p || !path) return fail(MCF_ERR_INVALID, "problem or path is NULL");
+  if (p->busy.load() > 0) return fail(MCF_ERR_BUSY, kOutstanding);
+  std::lock_guard<std::mutex> g(p->lock);
+  return device_load_state(p, path, device);
 }
 
 int mcf_solve(mcf_problem* p, const mcf_options* opts, mcf_result* res) {

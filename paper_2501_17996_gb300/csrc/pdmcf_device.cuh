@@ -63,56 +63,88 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_p<__nv_bfloat16, float
   return __float2bfloat16_rn(x);
 }
 
-// 16-byte vector loads/stores. "stream" = touched once per pass (evict-first in L2),
-// "keep" = read-only data that other CTAs re-read soon (default caching).
+// 16-byte (or, for 8-byte chunks, 8-byte) vector loads/stores. "stream" = touched once per
+// pass (evict-first), "keep" = read-only data that other CTAs re-read soon (default caching).
 template <typename T, int N>
 __device__ __forceinline__ void ld_keep(const T* p, T (&v)[N]) {
-  static_assert((N * sizeof(T)) % 16 == 0, "16-byte words");
-  constexpr int W = N * (int)sizeof(T) / 16;
+  static_assert((N * sizeof(T)) % 16 == 0 || N * sizeof(T) == 8, "8- or 16-byte words");
+  if constexpr (N * sizeof(T) == 8) {
+    uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+    memcpy(&v[0], &u, 8);
+  } else {
+    constexpr int W = N * (int)sizeof(T) / 16;
 #pragma unroll
-  for (int k = 0; k < W; ++k) {
-    uint4 u = __ldg(reinterpret_cast<const uint4*>(p) + k);
-    memcpy(&v[k * 16 / sizeof(T)], &u, 16);
+    for (int k = 0; k < W; ++k) {
+      uint4 u = __ldg(reinterpret_cast<const uint4*>(p) + k);
+      memcpy(&v[k * 16 / sizeof(T)], &u, 16);
+    }
   }
 }
 template <typename T, int N>
 __device__ __forceinline__ void ld_stream(const T* p, T (&v)[N]) {
-  constexpr int W = N * (int)sizeof(T) / 16;
+  if constexpr (N * sizeof(T) == 8) {
+    uint2 u = __ldcs(reinterpret_cast<const uint2*>(p));
+    memcpy(&v[0], &u, 8);
+  } else {
+    constexpr int W = N * (int)sizeof(T) / 16;
 #pragma unroll
-  for (int k = 0; k < W; ++k) {
-    uint4 u = __ldcs(reinterpret_cast<const uint4*>(p) + k);
-    memcpy(&v[k * 16 / sizeof(T)], &u, 16);
+    for (int k = 0; k < W; ++k) {
+      uint4 u = __ldcs(reinterpret_cast<const uint4*>(p) + k);
+      memcpy(&v[k * 16 / sizeof(T)], &u, 16);
+    }
   }
 }
 template <typename T, int N>
 __device__ __forceinline__ void ld_plain(const T* p, T (&v)[N]) {
-  constexpr int W = N * (int)sizeof(T) / 16;
+  if constexpr (N * sizeof(T) == 8) {
+    uint2 u = *reinterpret_cast<const uint2*>(p);
+    memcpy(&v[0], &u, 8);
+  } else {
+    constexpr int W = N * (int)sizeof(T) / 16;
 #pragma unroll
-  for (int k = 0; k < W; ++k) {
-    uint4 u = *(reinterpret_cast<const uint4*>(p) + k);
-    memcpy(&v[k * 16 / sizeof(T)], &u, 16);
+    for (int k = 0; k < W; ++k) {
+      uint4 u = *(reinterpret_cast<const uint4*>(p) + k);
+      memcpy(&v[k * 16 / sizeof(T)], &u, 16);
+    }
   }
 }
 template <typename T, int N>
 __device__ __forceinline__ void st_stream(T* p, const T (&v)[N]) {
-  constexpr int W = N * (int)sizeof(T) / 16;
+  if constexpr (N * sizeof(T) == 8) {
+    uint2 u;
+    memcpy(&u, &v[0], 8);
+    __stcs(reinterpret_cast<uint2*>(p), u);
+  } else {
+    constexpr int W = N * (int)sizeof(T) / 16;
 #pragma unroll
-  for (int k = 0; k < W; ++k) {
-    uint4 u;
-    memcpy(&u, &v[k * 16 / sizeof(T)], 16);
-    __stcs(reinterpret_cast<uint4*>(p) + k, u);
+    for (int k = 0; k < W; ++k) {
+      uint4 u;
+      memcpy(&u, &v[k * 16 / sizeof(T)], 16);
+      __stcs(reinterpret_cast<uint4*>(p) + k, u);
+    }
   }
 }
 template <typename T, int N>
 __device__ __forceinline__ void st_plain(T* p, const T (&v)[N]) {
-  constexpr int W = N * (int)sizeof(T) / 16;
+  if constexpr (N * sizeof(T) == 8) {
+    uint2 u;
+    memcpy(&u, &v[0], 8);
+    *reinterpret_cast<uint2*>(p) = u;
+  } else {
+    constexpr int W = N * (int)sizeof(T) / 16;
 #pragma unroll
-  for (int k = 0; k < W; ++k) {
-    uint4 u;
-    memcpy(&u, &v[k * 16 / sizeof(T)], 16);
-    *(reinterpret_cast<uint4*>(p) + k) = u;
+    for (int k = 0; k < W; ++k) {
+      uint4 u;
+      memcpy(&u, &v[k * 16 / sizeof(T)], 16);
+      *(reinterpret_cast<uint4*>(p) + k) = u;
+    }
   }
 }
+
+// Chunk width of the head-aligned kinds (bulk-copy and in-sum edge phases and their node
+// phase): 4 entries whatever the storage type of F, so a BF16 row has as many chunks as an
+// FP32 one (its F words are 8 bytes, its Y words 16) and the 512-thread groups stay as full.
+template <typename S> struct RowTraits { static constexpr int VW = 4; };
 
 
 // ------------------------------------------------------------------ TMA bulk copies + mbarrier
@@ -373,24 +405,38 @@ __device__ __forceinline__ P prox_log(P y, P beta, P w) {
 }
 
 // prox_{beta (-u)^*}(y) for u = w s^gamma: z = -t, t the root of
-// h(t) = t^(c1+1) (t + y) - c1 c2 (Sec. 2.3), c1 = gamma/(1-gamma),
+// h(t) = t^(c1+1) (t + y) - K (Sec. 2.3), c1 = gamma/(1-gamma), K = c1 c2,
 // c2 = beta (1/gamma - 1)(w gamma)^(1/(1-gamma)). h is increasing and convex on
-// [max(0,-y), inf); Newton from t_hi = max(0,-y) + (c1 c2)^(1/(c1+2)) (where h >= 0)
-// decreases monotonically to the root. gamma = 1/2 (c1 = 1) avoids transcendental calls.
-// (Starting from the previous dual instead saves iterations on average but not per warp,
-// whose slowest lane sets the time; measured slower.)
+// t >= t_lo = max(0, -y), so Newton from any point right of the root decreases
+// monotonically to it. The start is the smaller of two upper bounds of the root (derived):
+//   y >= 0: t^(c1+2) < K and t^(c1+1) y < K, so t < min(K^(1/(c1+2)), (K/y)^(1/(c1+1)));
+//   y < 0:  t = -y + d with t > |y| and t >= d, so d < min(K^(1/(c1+2)), K/|y|^(c1+1)).
+// In each regime the bound that applies is within a factor 4 of the root (the other term
+// of h is at most the dominant one there), so a handful of Newton steps reach FP
+// precision; the plain start t_lo + K^(1/(c1+2)) can be orders of magnitude too far right,
+// where each step only shrinks t by a constant factor. gamma = 1/2 (c1 = 1) is a cubic and
+// needs no transcendental calls beyond one cube root and one square root.
+template <typename P>
+__device__ __forceinline__ P newton_quot(P h, P dh) { return h / dh; }
+template <>
+__device__ __forceinline__ float newton_quot<float>(float h, float dh) {
+  return __fdividef(h, dh);   // a Newton correction: its last-bit rounding does not matter
+}
+
 template <typename P>
 __device__ __forceinline__ P prox_pow(P y, P beta, P w, P gamma) {
   const P tlo = y < P(0) ? -y : P(0);
   P t, k;
   if (gamma == P(0.5)) {
     k = beta * P(0.25) * w * w;                       // c1 c2 with c1 = 1
-    t = tlo + cbrt(k);
+    const P b1 = cbrt(k);
+    if (y >= P(0)) t = y > P(0) ? fmin(b1, sqrt(k / y)) : b1;
+    else t = tlo + fmin(b1, k / (y * y));
 #pragma unroll 1
     for (int it = 0; it < 60; ++it) {
       const P h = t * t * (t + y) - k;
       const P dh = t * (P(3) * t + P(2) * y);
-      P tn = t - h / dh;
+      P tn = t - newton_quot<P>(h, dh);
       tn = tn < tlo ? tlo : tn;
       if (!(tn < t)) break;
       t = tn;
@@ -398,13 +444,15 @@ __device__ __forceinline__ P prox_pow(P y, P beta, P w, P gamma) {
   } else {
     const P c1 = gamma / (P(1) - gamma);
     k = c1 * beta * (P(1) / gamma - P(1)) * pow(w * gamma, P(1) / (P(1) - gamma));
-    t = tlo + pow(k, P(1) / (c1 + P(2)));
+    const P b1 = pow(k, P(1) / (c1 + P(2)));
+    if (y >= P(0)) t = y > P(0) ? fmin(b1, pow(k / y, P(1) / (c1 + P(1)))) : b1;
+    else t = tlo + fmin(b1, k / pow(tlo, c1 + P(1)));
 #pragma unroll 1
     for (int it = 0; it < 60; ++it) {
       const P p = pow(t, c1);
       const P h = p * t * (t + y) - k;
       const P dh = p * ((c1 + P(2)) * t + (c1 + P(1)) * y);
-      P tn = t - h / dh;
+      P tn = t - newton_quot<P>(h, dh);
       tn = tn < tlo ? tlo : tn;
       if (!(tn < t)) break;
       t = tn;
@@ -415,22 +463,26 @@ __device__ __forceinline__ P prox_pow(P y, P beta, P w, P gamma) {
 
 template <typename P>
 __device__ __forceinline__ P util_value(int kind, P t, P w, P g) {      // u(t)
-  return kind == 0 ? w * log(t) : w * pow(t, g);
+  if (kind == 0) return w * log(t);
+  return g == P(0.5) ? w * sqrt(t) : w * pow(t, g);
 }
 template <typename P>
 __device__ __forceinline__ P util_grad(int kind, P t, P w, P g) {       // u'(t)
-  return kind == 0 ? w / t : w * g * pow(t, g - P(1));
+  if (kind == 0) return w / t;
+  return g == P(0.5) ? P(0.5) * w / sqrt(t) : w * g * pow(t, g - P(1));
 }
 // (-u)^*(y), y < 0: log: w log(w/(-y)) - w ; power: (1/g - 1)(w g)^(1/(1-g)) (-y)^(-g/(1-g))
 template <typename P>
 __device__ __forceinline__ P util_conj_neg(int kind, P y, P w, P g) {
   if (kind == 0) return w * log(w / (-y)) - w;
+  if (g == P(0.5)) return P(0.25) * w * w / (-y);
   return (P(1) / g - P(1)) * pow(w * g, P(1) / (P(1) - g)) * pow(-y, -g / (P(1) - g));
 }
 // (u')^{-1}(-y): the traffic whose marginal utility is -y
 template <typename P>
 __device__ __forceinline__ P util_traffic(int kind, P y, P w, P g) {
   if (kind == 0) return w / (-y);
+  if (g == P(0.5)) { const P x = w / (P(-2) * y); return x * x; }   // (w gamma/(-y))^2
   return pow(w * g / (-y), P(1) / (P(1) - g));
 }
 
@@ -697,21 +749,21 @@ __device__ __forceinline__ float2 shifted_q2(float2 f, float2 yh, float2 yt, flo
 // between them: mu' < min{q > mu} going right, mu' >= max{q <= mu} going left. Then
 // phi(mu') = 0 and mu' is returned without a confirming pass; the value is bitwise the one
 // the confirming pass would have accepted (same active set, same fixed-order sum).
-template <int GROUP, int VPT, int VW, typename P>
-__device__ __forceinline__ P project_mu(const P (&q)[VPT][VW], P c, P mu0, P lo,
-                                        GroupScratch<GROUP>& sh, int& phase) {
+// The entries are this thread's N values get(0..N-1), in a fixed order (the order of the
+// thread's partial sums, so every layout of the same values gives the same multiplier).
+template <int GROUP, int N, typename P, typename Get>
+__device__ __forceinline__ P project_mu_n(Get get, P c, P mu0, P lo, GroupScratch<GROUP>& sh,
+                                          int& phase) {
   auto eval = [&](P mu, P& s, int& cnt, P& amin, P& imax, auto want_imax) {
     constexpr bool IM = decltype(want_imax)::value;
     P ls = 0, am = (P)INFINITY, im = (P)(-INFINITY);
     int lc = 0;
 #pragma unroll
-    for (int v = 0; v < VPT; ++v)
-#pragma unroll
-      for (int u = 0; u < VW; ++u) {
-        const P x = q[v][u];
-        if (x > mu) { ls += x; ++lc; am = fmin(am, x); }
-        else if constexpr (IM) { im = fmax(im, x); }
-      }
+    for (int i = 0; i < N; ++i) {
+      const P x = get(i);
+      if (x > mu) { ls += x; ++lc; am = fmin(am, x); }
+      else if constexpr (IM) { im = fmax(im, x); }
+    }
     group_stats<GROUP, IM, P>(ls, lc, am, im, sh, phase);
     s = ls; cnt = lc; amin = am;
     if constexpr (IM) imax = im;
@@ -746,6 +798,22 @@ __device__ __forceinline__ P project_mu(const P (&q)[VPT][VW], P c, P mu0, P lo,
     eval(mu, s, cnt, amin, imax, without_imax{});
   }
   return mu;
+}
+
+template <int GROUP, int VPT, int VW, typename P>
+__device__ __forceinline__ P project_mu(const P (&q)[VPT][VW], P c, P mu0, P lo,
+                                        GroupScratch<GROUP>& sh, int& phase) {
+  return project_mu_n<GROUP, VPT * VW, P>([&](int i) { return q[i / VW][i % VW]; }, c, mu0, lo,
+                                          sh, phase);
+}
+
+// The same on entries held as FP32 pairs (q[v][p] = entries 2p and 2p+1 of chunk v).
+template <int GROUP, int VPT, int H>
+__device__ __forceinline__ float project_mu2(const float2 (&q)[VPT][H], float c, float mu0,
+                                             float lo, GroupScratch<GROUP>& sh, int& phase) {
+  return project_mu_n<GROUP, VPT * H * 2, float>(
+      [&](int i) { const float2 z = q[i / (2 * H)][(i % (2 * H)) / 2]; return (i & 1) ? z.y : z.x; },
+      c, mu0, lo, sh, phase);
 }
 
 // ------------------------------------------------------------------ edge phase
@@ -872,7 +940,8 @@ edge_kernel(IterArgs<P, S> a) {
 template <typename P, typename S, int VPT, int GROUP, int BLOCK, int MINB, bool PIN, bool CHECK>
 __global__ void __launch_bounds__(BLOCK, MINB)
 node_kernel(IterArgs<P, S> a) {
-  constexpr int VW = StoreTraits<S>::VW;
+  // the in-sum (PIN) variant pairs with the head-aligned edge phases and their chunk width
+  constexpr int VW = PIN ? RowTraits<S>::VW : StoreTraits<S>::VW;
   constexpr int GPB = BLOCK / GROUP;
   const int lane = threadIdx.x % GROUP;
   const int gid = blockIdx.x * GPB + threadIdx.x / GROUP;
@@ -1041,7 +1110,7 @@ template <typename S, int VPT, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1)
 edge_tma_kernel(IterArgs<float, S> a) {
   using P = float;
-  constexpr int VW = StoreTraits<S>::VW;
+  constexpr int VW = RowTraits<S>::VW;
   extern __shared__ __align__(128) unsigned char dyn[];
   __shared__ __align__(8) uint64_t full[2];
   __shared__ GroupScratch<BLOCK> sh;
@@ -1217,7 +1286,7 @@ template <typename P, typename S, int VPT, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 2)
 edge_insum_kernel(IterArgs<P, S> a) {
   static_assert(std::is_same<P, float>::value, "in-sum edge phase: FP32 iterates");
-  constexpr int VW = StoreTraits<S>::VW;
+  constexpr int VW = RowTraits<S>::VW;
   extern __shared__ __align__(16) unsigned char dyn_is[];
   P* yh_s = reinterpret_cast<P*>(dyn_is);
   P* sin_s = yh_s + a.ld;
@@ -1288,7 +1357,8 @@ edge_insum_kernel(IterArgs<P, S> a) {
     const S* fo = Fo + (size_t)e * a.ld;
     const P* yt = Y + (size_t)t * a.ld;
     const float2 nm0 = p2(-mu0), nm0l = p2(-mu0l);
-    P q[VPT][VW], f[VPT][VW];
+    constexpr int H = VW / 2;
+    float2 q[VPT][H], f[VPT][H];   // entry pairs: whole 64-bit registers for the packed ops
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
       const int ci = v * BLOCK + tid;
@@ -1297,7 +1367,7 @@ edge_insum_kernel(IterArgs<P, S> a) {
         P a1[VW], a2[VW], l1[VW], l2[VW];
         ld_stream<S, VW>(fo + ci * VW, fs);
         ld_plain<P, VW>(yh_s + ci * VW, a1);
-        ld_keep<P, VW>(yt + ci * VW, a2);
+        ld_stream<P, VW>(yt + ci * VW, a2);   // read once per edge: streamed, not kept in L1
         if (ylo) {
           ld_lo<VW>(ylo + (size_t)h * a.ld + ci * VW, l1);
           ld_lo<VW>(ylo + (size_t)t * a.ld + ci * VW, l2);
@@ -1309,17 +1379,16 @@ edge_insum_kernel(IterArgs<P, S> a) {
         for (int u = 0; u < VW; u += 2) {
           const float2 ff = make_float2(to_p<P>(fs[u]), to_p<P>(fs[u + 1]));
           const float2 dl = p2_sub(make_float2(l1[u], l1[u + 1]), make_float2(l2[u], l2[u + 1]));
-          const float2 qq = shifted_q2(ff, make_float2(a1[u], a1[u + 1]),
-                                       make_float2(a2[u], a2[u + 1]), dl, alpha, nm0, nm0l);
-          f[v][u] = ff.x; f[v][u + 1] = ff.y;
-          q[v][u] = qq.x; q[v][u + 1] = qq.y;
+          f[v][u / 2] = ff;
+          q[v][u / 2] = shifted_q2(ff, make_float2(a1[u], a1[u + 1]),
+                                   make_float2(a2[u], a2[u + 1]), dl, alpha, nm0, nm0l);
         }
       } else {
 #pragma unroll
-        for (int u = 0; u < VW; ++u) { f[v][u] = P(0); q[v][u] = shifted_floor<P>(mu0, mu0l); }
+        for (int h = 0; h < H; ++h) { f[v][h] = p2(0.f); q[v][h] = p2(shifted_floor<P>(mu0, mu0l)); }
       }
     }
-    const P mu = project_mu<BLOCK, VPT, VW, P>(q, c, P(0), shifted_floor<P>(mu0, mu0l), sh, phase);
+    const P mu = project_mu2<BLOCK, VPT, H>(q, c, P(0), shifted_floor<P>(mu0, mu0l), sh, phase);
     const float2 nmu2 = p2(-mu);
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
@@ -1330,8 +1399,8 @@ edge_insum_kernel(IterArgs<P, S> a) {
         ld_plain<P, VW>(sin_s + ci * VW, acc);
 #pragma unroll
         for (int u = 0; u < VW; u += 2) {
-          const float2 ff = make_float2(f[v][u], f[v][u + 1]);
-          const float2 t2 = p2_add(make_float2(q[v][u], q[v][u + 1]), nmu2);
+          const float2 ff = f[v][u / 2];
+          const float2 t2 = p2_add(q[v][u / 2], nmu2);
           const float2 fh = make_float2(fmaxf(t2.x, 0.f), fmaxf(t2.y, 0.f));   // (q - mu)_+
           const float2 st = p2_sub(fh, ff);                                      // f^ - f
           const float2 fnew = p2_fma(rho, st, ff);        // rho f^ + (1 - rho) f

@@ -56,6 +56,8 @@ int validate_options(const mcf_options* o);   // pdmcf_capi.cpp
 int device_solve(mcf_problem* p, const mcf_options* o, mcf_result* res,
                  mcf_kernel_times* kt = nullptr);
 int device_copy_outputs(mcf_problem* p, mcf_result* res);
+int device_save_state(mcf_problem* p, const char* path);
+int device_load_state(mcf_problem* p, const char* path, int device);
 void device_free(mcf_problem* p);
 int64_t device_bytes(const mcf_problem* p, int precision);
 }  // namespace pdmcf

@@ -83,6 +83,7 @@ class Server {
     t->id = next_id_++;
     t->p = p;
     t->opts = *o;
+    t->opts.check_log = nullptr;   // the caller's string need not outlive the call
     t->bytes = bytes;
     t->solo = !batch;
     t->t_submit = std::chrono::steady_clock::now();

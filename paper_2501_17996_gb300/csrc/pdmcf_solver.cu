@@ -12,6 +12,7 @@
 #include <chrono>
 #include <type_traits>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <limits>
 #include <string>
@@ -230,7 +231,7 @@ template <> const TmaTable<__nv_bfloat16>& get_tma_table<__nv_bfloat16>() { retu
 // (F row + Y row) in shared memory.
 template <typename S>
 static int setup_tma(DeviceState* d, int want) {
-  constexpr int VW = StoreTraits<S>::VW;
+  constexpr int VW = RowTraits<S>::VW;
   const int nchunks = (int)(d->ld / VW);
   int smem_optin = 0, sms = 0;
   CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d->device));
@@ -247,7 +248,7 @@ static int setup_tma(DeviceState* d, int want) {
   // row (edge + node 4.69 ms against 4.83 ms for the register kind); on renumbered networks
   // (kNN) the register kind's gathers hit L2 and it wins (4.67 against 4.97 ms). mcf_autotune
   // times every kind on the caller's problem.
-  else if (want < 0 && std::is_same<S, float>::value && !d->renumbered &&
+  else if (want < 0 && !d->renumbered &&
            (size_t)d->ld * sizeof(float) >= 8192 && 2 * (smem2 + 4096) <= (size_t)smem_optin) {
     for (int c = 0; c < NUM_TMA && t < 0; ++c)
       if (kTmaVpt[c] * TMA_BLOCK >= nchunks) { t = c; kind = 2; }
@@ -653,6 +654,35 @@ struct PhaseRule {
   bool skip_outputs = false;
 };
 
+// mcf_options.check_log: one JSON line per stop test (Sec. 3.1's convergence diagnostics).
+struct CheckLog {
+  FILE* f = nullptr;
+  explicit CheckLog(const char* path) { if (path && *path) f = std::fopen(path, "a"); }
+  ~CheckLog() { if (f) std::fclose(f); }
+};
+
+static void json_num(FILE* f, const char* key, double v, bool last = false) {
+  if (std::isfinite(v)) std::fprintf(f, "\"%s\": %.17g%s", key, v, last ? "" : ", ");
+  else std::fprintf(f, "\"%s\": null%s", key, last ? "" : ", ");
+}
+
+static void write_check_line(FILE* f, const DevScalars& h, int n, int m, int precision) {
+  std::fprintf(f, "{\"k\": %lld, ", (long long)h.k);
+  json_num(f, "omega", h.omega);
+  json_num(f, "r_over_nm", h.r / ((double)n * (double)m));
+  json_num(f, "rel_kkt", h.rel_kkt);
+  json_num(f, "rel_gap", h.rel_gap);
+  json_num(f, "rel_cons", h.rel_cons);
+  json_num(f, "rel_stat", h.rel_stat);
+  json_num(f, "utility", h.P);
+  json_num(f, "dual_bound", h.D);
+  json_num(f, "nonpos_frac", h.nonpos_frac);
+  std::fprintf(f, "\"omega_adapting\": %s, \"precision\": \"%s\"}\n",
+               (h.freeze >= 0 && h.freeze <= h.k) ? "false" : "true",
+               precision == MCF_FP64 ? "fp64" : (precision == MCF_BF16_F ? "bf16" : "fp32"));
+  std::fflush(f);
+}
+
 // mcf_test_withhold_next_copy: one pending request, taken by the next solve that runs the
 // bulk-copy edge phase.
 static std::atomic<int> g_withhold_request{0};
@@ -731,6 +761,12 @@ static int solve_t(mcf_problem* p, DeviceState* d, const mcf_options* o, mcf_res
     d->graph_lo = lo;
   }
   int parity = d->cur;
+  CheckLog log_file(o->check_log);
+  FILE* log = log_file.f;
+  if (o->check_log && *o->check_log && !log) {
+    set_error(std::string("cannot open the check log ") + o->check_log);
+    return MCF_ERR_INVALID;
+  }
   int64_t k = 0;
   double best_kkt = INFINITY;
   int since_best = 0;
@@ -768,6 +804,7 @@ static int solve_t(mcf_problem* p, DeviceState* d, const mcf_options* o, mcf_res
     any = true;
     d->cur = parity;
     d->valid = true;
+    if (log) write_check_line(log, h, n, m, d->precision);
     if (h.wait_timeout) {
       set_error("a bounded device-side wait timed out; the iteration was abandoned");
       d->valid = false;
@@ -1006,6 +1043,157 @@ void batch_finish_state(mcf_problem* p, int parity, const DevScalars& s, cudaStr
   p->omega = s.omega;
   cudaMemcpyAsync(d->sc, &s, sizeof(DevScalars), cudaMemcpyHostToDevice, st);
   cudaStreamSynchronize(st);
+}
+
+// ------------------------------------------------------------------ warm-state checkpoint
+// The resident warm tuple of Sec. 3.1 (F^{k-1/2}, Y^k with its compensated tail, the state
+// P = F^{k-1/2} A^T of the relaxation identity, the projection multipliers and omega) in the
+// device layout and internal numbering, written to or read from a host file through a
+// 64 MB pinned staging buffer.
+
+namespace {
+struct StateHeader {
+  char magic[8];          // "PDMCFWS1"
+  int32_t version;        // 1
+  int32_t n, m, ld, precision, lo_live;
+  double omega;
+  uint64_t topo_hash;     // FNV-1a over the internal (tail, head) order
+  uint64_t bytes[5];      // F, Y, Y tail, P, mu
+};
+
+uint64_t topo_hash(const Topology& t) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](const std::vector<int32_t>& v) {
+    for (int32_t x : v)
+      for (int b = 0; b < 4; ++b) { h ^= (uint64_t)((x >> (8 * b)) & 0xff); h *= 1099511628211ull; }
+  };
+  mix(t.e_tail);
+  mix(t.e_head);
+  mix(t.node_of);
+  return h;
+}
+
+constexpr size_t kStage = (size_t)64 << 20;
+}  // namespace
+
+int device_save_state(mcf_problem* p, const char* path) {
+  DeviceState* d = p->ds;
+  if (!d || !d->valid) {
+    set_error("the problem has no solved state to save");
+    return MCF_ERR_INVALID;
+  }
+  CK(cudaSetDevice(d->device));
+  const size_t n = d->n, m = d->m, ld = d->ld;
+  StateHeader h{};
+  std::memcpy(h.magic, "PDMCFWS1", 8);
+  h.version = 1;
+  h.n = d->n; h.m = d->m; h.ld = d->ld; h.precision = d->precision;
+  h.lo_live = d->lo_live ? 1 : 0;
+  h.omega = p->omega;
+  h.topo_hash = topo_hash(p->topo);
+  const void* src[5] = {d->F[d->cur], d->Y[d->cur], d->lo_live ? d->Ylo[d->cur] : nullptr, d->Pm, d->mu};
+  const uint64_t bytes[5] = {m * ld * d->sbytes, n * ld * d->pbytes, d->lo_live ? n * ld * 2 : 0,
+                             n * ld * d->pbytes, 2 * m * d->pbytes};
+  std::memcpy(h.bytes, bytes, sizeof(bytes));
+  FILE* f = std::fopen(path, "wb");
+  if (!f) {
+    set_error(std::string("cannot open ") + path + " for writing");
+    return MCF_ERR_INVALID;
+  }
+  char* stage = nullptr;
+  if (cudaMallocHost((void**)&stage, kStage) != cudaSuccess) {
+    std::fclose(f);
+    cudaGetLastError();
+    set_error("pinned host allocation failed");
+    return MCF_ERR_OOM;
+  }
+  bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1;
+  cudaError_t e = cudaDeviceSynchronize();   // the state is complete only after the solve
+  for (int a = 0; a < 5 && ok && e == cudaSuccess; ++a)
+    for (uint64_t off = 0; off < bytes[a] && ok && e == cudaSuccess; off += kStage) {
+      const size_t len = (size_t)std::min<uint64_t>(kStage, bytes[a] - off);
+      e = cudaMemcpy(stage, (const char*)src[a] + off, len, cudaMemcpyDeviceToHost);
+      ok = e == cudaSuccess && std::fwrite(stage, 1, len, f) == len;
+    }
+  cudaFreeHost(stage);
+  const bool closed = std::fclose(f) == 0;
+  if (e != cudaSuccess) {
+    set_error(std::string("CUDA error ") + cudaGetErrorString(e) + " while saving the state");
+    return MCF_ERR_CUDA;
+  }
+  if (!ok || !closed) {
+    set_error(std::string("write to ") + path + " failed");
+    return MCF_ERR_INVALID;
+  }
+  return MCF_OK;
+}
+
+int device_load_state(mcf_problem* p, const char* path, int device) {
+  FILE* f = std::fopen(path, "rb");
+  if (!f) {
+    set_error(std::string("cannot open ") + path);
+    return MCF_ERR_INVALID;
+  }
+  StateHeader h{};
+  if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, "PDMCFWS1", 8) != 0 ||
+      h.version != 1) {
+    std::fclose(f);
+    set_error(std::string(path) + " is not a PDMCF warm-state file");
+    return MCF_ERR_INVALID;
+  }
+  if (h.n != p->n || h.m != p->m || h.ld != (int)ld_of(p->n) || h.topo_hash != topo_hash(p->topo) ||
+      (h.precision != MCF_FP32 && h.precision != MCF_FP64 && h.precision != MCF_BF16_F)) {
+    std::fclose(f);
+    set_error("the saved state belongs to a different network");
+    return MCF_ERR_INVALID;
+  }
+  if (p->ds && (p->ds->precision != h.precision || p->ds->device != device)) device_free(p);
+  if (!p->ds) {
+    int rc = alloc_state(p, h.precision, device, -1, nullptr, &p->ds);
+    if (rc != MCF_OK) { std::fclose(f); return rc; }
+  }
+  DeviceState* d = p->ds;
+  CK(cudaSetDevice(d->device));
+  const size_t n = d->n, m = d->m, ld = d->ld;
+  const uint64_t want[5] = {m * ld * d->sbytes, n * ld * d->pbytes, h.lo_live ? n * ld * 2 : 0,
+                            n * ld * d->pbytes, 2 * m * d->pbytes};
+  if (std::memcmp(want, h.bytes, sizeof(want)) != 0 || (h.lo_live && !d->Ylo[0])) {
+    std::fclose(f);
+    set_error("the saved state's array sizes do not match this problem");
+    return MCF_ERR_INVALID;
+  }
+  void* dst[5] = {d->F[0], d->Y[0], h.lo_live ? d->Ylo[0] : nullptr, d->Pm, d->mu};
+  char* stage = nullptr;
+  if (cudaMallocHost((void**)&stage, kStage) != cudaSuccess) {
+    std::fclose(f);
+    cudaGetLastError();
+    set_error("pinned host allocation failed");
+    return MCF_ERR_OOM;
+  }
+  d->valid = false;
+  bool ok = true;
+  cudaError_t e = cudaDeviceSynchronize();
+  for (int a = 0; a < 5 && ok && e == cudaSuccess; ++a)
+    for (uint64_t off = 0; off < want[a] && ok && e == cudaSuccess; off += kStage) {
+      const size_t len = (size_t)std::min<uint64_t>(kStage, want[a] - off);
+      ok = std::fread(stage, 1, len, f) == len;
+      if (ok) e = cudaMemcpy((char*)dst[a] + off, stage, len, cudaMemcpyHostToDevice);
+    }
+  cudaFreeHost(stage);
+  std::fclose(f);
+  if (e != cudaSuccess) {
+    set_error(std::string("CUDA error ") + cudaGetErrorString(e) + " while loading the state");
+    return MCF_ERR_CUDA;
+  }
+  if (!ok) {
+    set_error(std::string(path) + " is truncated");
+    return MCF_ERR_INVALID;
+  }
+  d->cur = 0;
+  d->lo_live = h.lo_live != 0;
+  d->valid = true;
+  p->omega = h.omega;
+  return MCF_OK;
 }
 
 int device_solve(mcf_problem* p, const mcf_options* o, mcf_result* res, mcf_kernel_times* kt) {

@@ -194,3 +194,21 @@ def test_renumbering_recovers_grid_locality(lib):
     assert renumbered
     span = np.abs(node_of[tail].astype(np.int64) - node_of[head]).mean()
     assert span <= 2 * side, span
+
+
+def test_warm_state_file_errors_without_a_device(lib, tmp_path):
+    """Saving needs a solved state; loading checks the file before touching the device."""
+    from paper_2501_17996_gb300 import instances as I
+
+    with lib.Problem(I.tiny(0)) as p:
+        with pytest.raises(lib.MCFError) as ei:
+            p.save_state(str(tmp_path / "none.pdmcf"))
+        assert ei.value.code == lib.MCF_ERR_INVALID and "no solved state" in lib.mcf_last_error()
+        with pytest.raises(lib.MCFError) as ei:
+            p.load_state(str(tmp_path / "missing.pdmcf"))
+        assert ei.value.code == lib.MCF_ERR_INVALID
+        bad = tmp_path / "bad.pdmcf"
+        bad.write_bytes(b"not a state file at all, not even close" * 4)
+        with pytest.raises(lib.MCFError) as ei:
+            p.load_state(str(bad))
+        assert ei.value.code == lib.MCF_ERR_INVALID and "not a PDMCF" in lib.mcf_last_error()

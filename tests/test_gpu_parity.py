@@ -45,8 +45,9 @@ def shapes_for(lib, inst, precision):
     vw = {"fp32": 4, "fp64": 2, "bf16": 8}[precision]
     nchunks = ((inst.n + 7) // 8 * 8) // vw
     out = []
+    rows = ((inst.n + 7) // 8 * 8) // 4     # kinds 1 and 2 use 4-entry chunks
     for s, (g, v, b, piped) in enumerate(lib.mcf_shape_info()):
-        if g * v >= nchunks and not (precision == "fp64" and (s >= 10 or piped)):
+        if g * v >= (rows if piped else nchunks) and not (precision == "fp64" and (s >= 10 or piped)):
             out.append(s)
     return out
 
