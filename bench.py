@@ -458,29 +458,52 @@ def run_batched(args, rank, world, local_rank):
     rc, res = B.mcf_solve_batch(probs, B.mcf_options_default(**kw))
     t_batch = time.perf_counter() - t0
     iters = [r["iters"] for r in res]
+    # the same 64 solves submitted together (continuous batching): each one's completion
+    # time from the common start
     t0 = time.perf_counter()
-    lat = []
+    pending = {p.submit(**kw): i for i, p in enumerate(probs)}
+    done_at = [None] * len(probs)
+    status = [None] * len(probs)
+    while pending:
+        for tk in list(pending):
+            r = B.mcf_poll(tk)
+            if r is not None:
+                i = pending.pop(tk)
+                done_at[i] = time.perf_counter() - t0
+                status[i] = r["status"]
+        time.sleep(0.0005)
+    t_served = max(done_at)
+    # one at a time from the same common start: solve i completes after solves 0..i
+    t0 = time.perf_counter()
+    seq_done = []
     for p in probs:
-        t1 = time.perf_counter()
         p.solve(want_T=False, **kw)
-        lat.append(time.perf_counter() - t1)
-    t_seq = time.perf_counter() - t0
+        seq_done.append(time.perf_counter() - t0)
+    t_seq = seq_done[-1]
     for p in probs:
         p.close()
     if rank != 0:
         return
+
+    def pct(x):
+        return {"p50_s": float(np.percentile(x, 50)), "p99_s": float(np.percentile(x, 99)),
+                "max_s": float(np.max(x))}
+
     line = {
         "metric": METRIC, "value": len(insts) / t_batch, "unit": "solves/s", "n_gpus": world,
         "steps": 1, "warmup": 1, "ms_per_step": t_batch * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "batched: 64 instances, n~U[50,400], out-degree~U[4,16], "
                                "c~U[1,10], half log / half power gamma~U[0.3,0.7]",
-                   "stop": "rel_kkt < 1e-4", "k_check": args.k_check},
+                   "stop": "rel_kkt < 1e-4", "k_check": args.k_check,
+                   "latency": "completion time of each solve from the common start of its arm"},
         "batched": {"seconds": t_batch, "solves_per_s": len(insts) / t_batch, "rc": rc,
                     "iters_total": int(sum(iters)), "iters_max": int(max(iters)),
-                    "all_converged": all(r["status"] == 0 for r in res)},
-        "one_at_a_time": {"seconds": t_seq, "solves_per_s": len(insts) / t_seq,
-                          "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99))},
+                    "all_converged": all(r["status"] == 0 for r in res),
+                    "note": "mcf_solve_batch returns when every solve is done"},
+        "submitted_together": {"seconds": t_served, "solves_per_s": len(insts) / t_served,
+                               "all_converged": all(s_ == 0 for s_ in status), **pct(done_at)},
+        "one_at_a_time": {"seconds": t_seq, "solves_per_s": len(insts) / t_seq, **pct(seq_done)},
         "speedup": t_seq / t_batch,
     }
     print(json.dumps(line), flush=True)
@@ -580,10 +603,15 @@ def run_served(args, rank, world, local_rank):
                 break
         wall = time.perf_counter() - t0
         got = [x for x in lat if x is not None]
-        return {"completed": len(got), "offered": len(arrivals), "wall_s": wall,
-                "solves_per_s": len(got) / wall if wall > 0 else None,
-                "p50_s": float(np.percentile(got, 50)) if got else None,
-                "p99_s": float(np.percentile(got, 99)) if got else None,
+        # a request that did not finish counts as slower than any that did: its latency is
+        # at least the time it waited (window + drain limit - arrival)
+        lim = [x if x is not None else wall - arrivals[i][0] for i, x in enumerate(lat)]
+        unfinished = len(lat) - len(got)
+        return {"completed": len(got), "offered": len(arrivals), "unfinished": unfinished,
+                "wall_s": wall, "solves_per_s": len(got) / wall if wall > 0 else None,
+                "p50_s": float(np.percentile(lim, 50)) if lim else None,
+                "p99_s": float(np.percentile(lim, 99)) if lim else None,
+                "p99_is_lower_bound": unfinished > 0,
                 "mean_iters": float(np.mean(iters)) if iters else None}
 
     served = run_trace("served")

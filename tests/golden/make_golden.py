@@ -19,7 +19,7 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 from oracle import pdmcf as O  # noqa: E402
 from paper_2501_17996_gb300 import instances as I  # noqa: E402
 
-PARALLEL = {"slice_s0_kkt1e-4"}   # cases run with oracle.parallel's step
+PARALLEL = {"slice_s0_kkt1e-4", "slice_s0_kkt1e-6"}   # cases run with oracle.parallel's step
 
 CASES = {
     # name: (instance factory, rel_kkt tolerance, iterations between stop tests)
@@ -32,6 +32,8 @@ CASES = {
     "midpow_s0_kkt1e-4": (lambda: I.large(0, n=100), 1e-4, 50),
     # the large recipe at n = 1000; its primal and dual values bracket the optimum U*
     "slice_s0_kkt1e-4": (lambda: I.large_slice(0), 1e-4, 50),
+    # the same, close to the optimum: the reference T* for the slice
+    "slice_s0_kkt1e-6": (lambda: I.large_slice(0), 1e-6, 50),
 }
 
 
