@@ -423,7 +423,9 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "alg_bytes_per_launch": alg[dom],
-                     "ms_per_launch": dom_ms},
+                     "ms_per_launch": dom_ms,
+                     # the kernel's own DRAM bytes (ncu) over the same event time
+                     "traffic_frac": (traffic / (dom_ms / 1e3) / 1e9 / peak) if traffic else None},
         "hbm": {"iteration_floor_gbs": alg["iteration_floor"] / (iter_ms / 1e3) / 1e9,
                 "iteration_alg_gbs": (alg["edge"] + alg["node"]) / (iter_ms / 1e3) / 1e9,
                 "peak_gbs": peak, "kernels": per_kernel},
