@@ -604,6 +604,10 @@ def run_served(args, rank, world, local_rank):
             if time.perf_counter() - t0 > args.window + args.drain_limit:
                 break
         wall = time.perf_counter() - t0
+        for tk in list(pending):   # past the drain limit: cancel and collect what still runs
+            B.mcf_cancel(tk)
+            B.mcf_wait(tk, -1)
+            pending.pop(tk)
         got = [x for x in lat if x is not None]
         # a request that did not finish counts as slower than any that did: its latency is
         # at least the time it waited (window + drain limit - arrival)
