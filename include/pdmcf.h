@@ -186,6 +186,12 @@ int mcf_problem_size(const mcf_problem* p, int32_t* n, int32_t* m);
  * (node_of is then the identity), or a negative error code. */
 int mcf_problem_node_order(const mcf_problem* p, int32_t* node_of);
 
+/* The library's internal edge order: edges sorted by head (internal numbering), so each
+ * node's in-edges are one contiguous block of rows of the edge-major F.
+ *   edge_of  m int32 (host): edge_of[internal edge e] = the caller's edge index
+ * It is also the row order of F in a file written by mcf_save_state. Returns MCF_OK. */
+int mcf_problem_edge_order(const mcf_problem* p, int32_t* edge_of);
+
 /* Device bytes one solve of this problem needs at the given precision. */
 int64_t mcf_problem_device_bytes(const mcf_problem* p, int precision);
 

@@ -68,7 +68,7 @@ KERNEL_KINDS = ("edge", "node", "check", "scalar")
 
 SYMBOLS = [
     "mcf_create_problem", "mcf_update_capacities", "mcf_update_weights",
-    "mcf_destroy_problem", "mcf_problem_size", "mcf_problem_node_order",
+    "mcf_destroy_problem", "mcf_problem_size", "mcf_problem_node_order", "mcf_problem_edge_order",
     "mcf_problem_device_bytes",
     "mcf_options_default", "mcf_solve", "mcf_solve_timed", "mcf_solve_batch", "mcf_autotune",
     "mcf_submit", "mcf_poll", "mcf_wait",
@@ -96,6 +96,7 @@ def _load() -> C.CDLL:
         "mcf_destroy_problem": (C.c_int, [P]),
         "mcf_problem_size": (C.c_int, [P, ip, ip]),
         "mcf_problem_node_order": (C.c_int, [P, ip]),
+        "mcf_problem_edge_order": (C.c_int, [P, ip]),
         "mcf_problem_device_bytes": (C.c_int64, [P, C.c_int]),
         "mcf_options_default": (None, [C.POINTER(mcf_options)]),
         "mcf_solve": (C.c_int, [P, C.POINTER(mcf_options), C.POINTER(mcf_result)]),
@@ -437,6 +438,14 @@ class Problem:
         if rc < 0:
             raise MCFError(rc, "mcf_problem_node_order")
         return bool(rc), out
+
+    def edge_order(self) -> np.ndarray:
+        """edge_of[internal edge] = the caller's edge index (rows of F in a saved state)."""
+        out = np.empty(self.m, dtype=np.int32)
+        rc = LIB.mcf_problem_edge_order(self.h, out.ctypes.data_as(C.POINTER(C.c_int32)))
+        if rc != MCF_OK:
+            raise MCFError(rc, "mcf_problem_edge_order")
+        return out
 
     def close(self):
         if self.h:

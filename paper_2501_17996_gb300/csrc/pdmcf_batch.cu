@@ -17,6 +17,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pdmcf_batch_engine.h"
 
 namespace pdmcf {
@@ -313,6 +315,13 @@ void BatchEngine::destroy_graphs() {
 }
 
 int BatchEngine::step(int iters) {
+  nvtxRangePushA("pdmcf batched chunk");
+  const int rc = step_impl(iters);
+  nvtxRangePop();
+  return rc;
+}
+
+int BatchEngine::step_impl(int iters) {
   BCK(cudaSetDevice(device_));
   if (lists_dirty_) {
     int rc = upload_lists();

@@ -60,6 +60,7 @@ class BatchEngine {
   static int64_t extra_bytes(const mcf_problem* p);   // engine buffers per instance
 
  private:
+  int step_impl(int iters);
   int upload_lists();
   int launch_iteration(cudaStream_t st);
   void destroy_graphs();

@@ -344,6 +344,12 @@ int mcf_problem_node_order(const mcf_problem* p, int32_t* node_of) {
   return p->topo.node_of.empty() ? 0 : 1;
 }
 
+int mcf_problem_edge_order(const mcf_problem* p, int32_t* edge_of) {
+  if (!p || !edge_of) return fail(MCF_ERR_INVALID, "problem or edge_of is NULL");
+  for (int e = 0; e < p->m; ++e) edge_of[e] = p->topo.perm[e];
+  return MCF_OK;
+}
+
 int64_t mcf_problem_device_bytes(const mcf_problem* p, int precision) {
   if (!p) return fail(MCF_ERR_INVALID, "problem is NULL");
   return device_bytes(p, precision);

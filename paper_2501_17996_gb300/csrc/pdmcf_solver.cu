@@ -18,6 +18,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pdmcf_batch.cuh"
 #include "pdmcf_internal.h"
 #include "pdmcf_kernels.h"
@@ -94,6 +96,13 @@ __global__ void fhat_kernel(const S* Fo, const P* Y, const __nv_bfloat16* Ylo, c
 }
 
 // ------------------------------------------------------------------ device state
+
+// NVTX ranges (host side) for profilers: a solve, each chunk of k_check iterations and, in
+// timed solves, each phase's launch. Without an attached tool they cost a branch.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 struct DeviceState {
   int device = -1, precision = -1;
@@ -567,13 +576,20 @@ static cudaError_t launch_iteration_timed(DeviceState* d, IterArgs<P, S> a, int 
   void* kargs[] = {&a};
   cudaError_t e;
   if (pool.used == 0) cudaEventRecord(pool.next(-1), st);
-  e = launch_phase<P, S>(d, kargs, 0, check, st);
+  {
+    NvtxRange r("pdmcf edge phase");
+    e = launch_phase<P, S>(d, kargs, 0, check, st);
+  }
   if (e != cudaSuccess) return e;
   cudaEventRecord(pool.next(0), st);
-  e = launch_phase<P, S>(d, kargs, 1, check, st);
+  {
+    NvtxRange r("pdmcf node phase");
+    e = launch_phase<P, S>(d, kargs, 1, check, st);
+  }
   if (e != cudaSuccess) return e;
   cudaEventRecord(pool.next(1), st);
   if (check) {
+    NvtxRange r("pdmcf check phase");
     e = cudaLaunchKernel((const void*)T.check[d->shape], dim3(d->grid_check), dim3(d->block), kargs, 0, st);
     if (e != cudaSuccess) return e;
     cudaEventRecord(pool.next(2), st);
@@ -777,7 +793,10 @@ static int solve_t(mcf_problem* p, DeviceState* d, const mcf_options* o, mcf_res
   int status = MCF_ERR_NOT_CONVERGED;
   if (o->stop_mode == MCF_STOP_NONE) status = MCF_OK;
   bool any = false;
+  NvtxRange solve_range(d->precision == MCF_FP64 ? "pdmcf solve fp64"
+                        : d->precision == MCF_BF16_F ? "pdmcf solve bf16" : "pdmcf solve fp32");
   while (k < max_iters) {
+    NvtxRange chunk_range("pdmcf chunk");
     const int64_t chunk = std::min<int64_t>(kc - (k % kc), max_iters - k);
     const bool stall_first = withhold && k == 0;
     if (use_graphs && chunk == kc && !stall_first) {
