@@ -889,10 +889,23 @@ edge_kernel(IterArgs<P, S> a) {
             for (int u = 0; u < VW; ++u) dl[u] = l1[u] - l2[u];
           }
         }
+        if constexpr (std::is_same<P, float>::value) {   // packed pairs, same rounding
 #pragma unroll
-        for (int u = 0; u < VW; ++u) {
-          f[v][u] = to_p<P>(fs[u]);
-          q[v][u] = shifted_q<P>(f[v][u], a1[u], a2[u], dl[u], alpha, mu0, mu0l);
+          for (int u = 0; u < VW; u += 2) {
+            const float2 ff = make_float2(to_p<P>(fs[u]), to_p<P>(fs[u + 1]));
+            const float2 qq = shifted_q2(ff, make_float2(a1[u], a1[u + 1]),
+                                         make_float2(a2[u], a2[u + 1]),
+                                         make_float2(dl[u], dl[u + 1]), p2(alpha), p2(-mu0),
+                                         p2(-mu0l));
+            f[v][u] = ff.x; f[v][u + 1] = ff.y;
+            q[v][u] = qq.x; q[v][u + 1] = qq.y;
+          }
+        } else {
+#pragma unroll
+          for (int u = 0; u < VW; ++u) {
+            f[v][u] = to_p<P>(fs[u]);
+            q[v][u] = shifted_q<P>(f[v][u], a1[u], a2[u], dl[u], alpha, mu0, mu0l);
+          }
         }
       } else {
 #pragma unroll
@@ -906,16 +919,33 @@ edge_kernel(IterArgs<P, S> a) {
       const int ci = v * GROUP + lane;
       if (ci < nchunks) {
         S out[VW];
+        if constexpr (std::is_same<P, float>::value) {
+          // f_new = f + rho (f^ - f) and (f^ - f)^2 on packed pairs; rho^2 is applied per edge
+          float2 sq = p2(0.f);
 #pragma unroll
-        for (int u = 0; u < VW; ++u) {
-          const P fh = q[v][u] > mu ? q[v][u] - mu : P(0);
-          const P fnew = rho * fh + (P(1) - rho) * f[v][u];
-          out[u] = from_p<S, P>(fnew);
-          // Delta_F uses the step rho (f^ - f) itself: the rounding of the stored iterate
-          // (about one ulp per entry) would otherwise swamp Delta_F near convergence and
-          // drive the primal weight rule
-          const P d = rho * (fh - f[v][u]);
-          dloc = fma(d, d, dloc);
+          for (int u = 0; u < VW; u += 2) {
+            const float2 ff = make_float2(f[v][u], f[v][u + 1]);
+            const float2 t2 = p2_add(make_float2(q[v][u], q[v][u + 1]), p2(-mu));
+            const float2 fh = make_float2(fmaxf(t2.x, 0.f), fmaxf(t2.y, 0.f));
+            const float2 st = p2_sub(fh, ff);
+            const float2 fnew = p2_fma(p2(rho), st, ff);
+            sq = p2_fma(st, st, sq);
+            out[u] = from_p<S, P>(fnew.x);
+            out[u + 1] = from_p<S, P>(fnew.y);
+          }
+          dloc += rho * rho * (sq.x + sq.y);
+        } else {
+#pragma unroll
+          for (int u = 0; u < VW; ++u) {
+            const P fh = q[v][u] > mu ? q[v][u] - mu : P(0);
+            const P fnew = rho * fh + (P(1) - rho) * f[v][u];
+            out[u] = from_p<S, P>(fnew);
+            // Delta_F uses the step rho (f^ - f) itself: the rounding of the stored iterate
+            // (about one ulp per entry) would otherwise swamp Delta_F near convergence and
+            // drive the primal weight rule
+            const P d = rho * (fh - f[v][u]);
+            dloc = fma(d, d, dloc);
+          }
         }
         st_stream<S, VW>(Fn + (size_t)e * a.ld + ci * VW, out);
       }

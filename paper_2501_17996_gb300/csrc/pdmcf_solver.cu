@@ -128,6 +128,7 @@ struct DeviceState {
   size_t tma_smem = 0;
   void* Pin = nullptr;
   int32_t* cta_ptr = nullptr;
+  int32_t* node_map = nullptr;   // caller node -> internal node (boundary layouts)
   int cur = 0;
   bool valid = false;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -177,7 +178,7 @@ static void free_state(DeviceState* d) {
   void* bufs[] = {d->F[0], d->F[1], d->Y[0], d->Y[1], d->Ylo[0], d->Ylo[1], d->Pm, d->W, d->G, d->mu, d->cap,
                   d->That, d->Uprime, d->Yhat, d->e_tail, d->e_head, d->in_ptr,
                   d->out_ptr, d->out_idx, d->part_edge, d->part_node, d->part_check, d->sc,
-                  d->Pin, d->cta_ptr};
+                  d->Pin, d->cta_ptr, d->node_map};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (d->sc_host) cudaFreeHost(d->sc_host);
@@ -206,26 +207,112 @@ int64_t device_bytes(const mcf_problem* p, int precision) {
 }
 
 // Upload c, w (transposed to Wt[j][i] = w_ij) and per-pair gamma in precision P.
+// ------------------------------------------------------------------ boundary layouts
+// The caller's arrays are row-major n x n (or n x m for F) in doubles; the device keeps
+// source-major rows in its own node numbering. Both conversions run on the device as tiled
+// transposes (32 x 32 tiles through shared memory, so reads and writes are coalesced), over
+// chunks of rows so the staging buffer stays small.
+
+// out[r][c] (r in [r0, r0 + rows), c < ncols, doubles) = in[rowmap[c]][colmap[r]]
+template <typename P>
+__global__ void gather_out_kernel(const P* __restrict__ in, size_t ld_in,
+                                  const int32_t* __restrict__ rowmap,
+                                  const int32_t* __restrict__ colmap, double* __restrict__ out,
+                                  int r0, int rows, int ncols) {
+  __shared__ double tile[32][33];
+  const int rb = blockIdx.y * 32, cb = blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int k = ty; k < 32; k += 8) {          // read: consecutive threads -> consecutive r
+    const int r = rb + tx, c = cb + k;
+    if (r < rows && c < ncols)
+      tile[k][tx] = (double)in[(size_t)rowmap[c] * ld_in + colmap[r0 + r]];
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {          // write: consecutive threads -> consecutive c
+    const int r = rb + k, c = cb + tx;
+    if (r < rows && c < ncols) out[(size_t)r * ncols + c] = tile[tx][k];
+  }
+}
+
+// W[node(c)][node(r0 + r)] = in[r][c] for the chunk's caller rows r (diag: `diag`)
+template <typename P>
+__global__ void scatter_in_kernel(const double* __restrict__ in, int r0, int rows, int n,
+                                  const int32_t* __restrict__ node, P* __restrict__ W,
+                                  size_t ld, P diag) {
+  __shared__ double tile[32][33];
+  const int rb = blockIdx.y * 32, cb = blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int k = ty; k < 32; k += 8) {          // read along c
+    const int r = rb + k, c = cb + tx;
+    if (r < rows && c < n) tile[k][tx] = in[(size_t)r * n + c];
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {          // write along r (the internal column)
+    const int r = rb + tx, c = cb + k;
+    if (r < rows && c < n) {
+      const int i = r0 + r;
+      W[(size_t)node[c] * ld + node[i]] = (i == c) ? diag : (P)tile[tx][k];
+    }
+  }
+}
+
+// Node map (caller node -> internal node) on the device, uploaded once per state.
+static int ensure_node_map(mcf_problem* p, DeviceState* d, cudaStream_t st) {
+  if (d->node_map) return MCF_OK;
+  std::vector<int32_t> nm(d->n);
+  for (int i = 0; i < d->n; ++i) nm[i] = p->topo.node(i);
+  if (cudaMalloc((void**)&d->node_map, (size_t)d->n * 4) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("device allocation failed");
+    return MCF_ERR_OOM;
+  }
+  CK(cudaMemcpyAsync(d->node_map, nm.data(), (size_t)d->n * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return MCF_OK;
+}
+
+// Rows of the caller's n x n array per staging chunk (about 64 MB of doubles).
+static int chunk_rows(int n, int cols) {
+  const size_t per = (size_t)cols * sizeof(double);
+  return (int)std::max<size_t>(32, std::min<size_t>((size_t)n, ((size_t)64 << 20) / per));
+}
+
+// Upload c and w (placed as Wt[node(j)][node(i)] = w_ij) and per-pair gamma in precision P.
 template <typename P>
 static int upload_data(mcf_problem* p, DeviceState* d, cudaStream_t st) {
-  const int n = p->n, m = p->m, ld = d->ld;
+  const int n = p->n, m = p->m;
+  const size_t ld = d->ld;
   std::vector<P> cap(m);
   for (int e = 0; e < m; ++e) cap[e] = (P)p->cap[p->topo.perm[e]];
   CK(cudaMemcpyAsync(d->cap, cap.data(), m * sizeof(P), cudaMemcpyHostToDevice, st));
-  const Topology& tp = p->topo;   // caller (i, j) -> internal row node(j), column node(i)
-  std::vector<P> wt((size_t)n * ld, P(0));
-  for (int j = 0; j < n; ++j)
-    for (int i = 0; i < n; ++i)
-      if (i != j) wt[(size_t)tp.node(j) * ld + tp.node(i)] = (P)p->w[(size_t)i * n + j];
-  CK(cudaMemcpyAsync(d->W, wt.data(), wt.size() * sizeof(P), cudaMemcpyHostToDevice, st));
-  if (d->G) {
-    for (int j = 0; j < n; ++j)
-      for (int i = 0; i < n; ++i)
-        wt[(size_t)tp.node(j) * ld + tp.node(i)] =
-            (i != j) ? (P)p->gamma_mat[(size_t)i * n + j] : P(0.5);
-    CK(cudaMemcpyAsync(d->G, wt.data(), wt.size() * sizeof(P), cudaMemcpyHostToDevice, st));
+  int rc = ensure_node_map(p, d, st);
+  if (rc != MCF_OK) return rc;
+  const int rows = chunk_rows(n, n);
+  double* stage = nullptr;
+  if (cudaMalloc((void**)&stage, (size_t)rows * n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("device allocation for the weight upload failed");
+    return MCF_ERR_OOM;
   }
-  CK(cudaStreamSynchronize(st));   // host staging vectors die at return
+  auto place = [&](const double* src, void* dst, P diag) -> cudaError_t {
+    cudaError_t e = cudaMemsetAsync(dst, 0, (size_t)n * ld * sizeof(P), st);   // pads stay 0
+    for (int r0 = 0; r0 < n && e == cudaSuccess; r0 += rows) {
+      const int nr = std::min(rows, n - r0);
+      e = cudaMemcpyAsync(stage, src + (size_t)r0 * n, (size_t)nr * n * sizeof(double),
+                          cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) break;
+      const dim3 grid((n + 31) / 32, (nr + 31) / 32);
+      scatter_in_kernel<P><<<grid, dim3(32, 8), 0, st>>>(stage, r0, nr, n, d->node_map,
+                                                         (P*)dst, ld, diag);
+      e = cudaGetLastError();
+    }
+    return e;
+  };
+  cudaError_t e = place(p->w.data(), d->W, P(0));
+  if (e == cudaSuccess && d->G) e = place(p->gamma_mat.data(), d->G, P(0.5));
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // the stage and the host vectors
+  cudaFree(stage);
+  CK(e);
   p->data_dirty = false;
   return MCF_OK;
 }
@@ -252,13 +339,15 @@ static int setup_tma(DeviceState* d, int want) {
   int t = -1, kind = 0;
   if (want >= NUM_SHAPES + NUM_TMA) { t = want - NUM_SHAPES - NUM_TMA; kind = 2; }
   else if (want >= NUM_SHAPES) { t = want - NUM_SHAPES; kind = 1; }
-  // automatic choice, measured at n = 10^4 (FP32): on networks without node locality
-  // (random chords, m = 10^5) the in-sum kind saves the node phase's second read of each F
-  // row (edge + node 4.69 ms against 4.83 ms for the register kind); on renumbered networks
-  // (kNN) the register kind's gathers hit L2 and it wins (4.67 against 4.97 ms). mcf_autotune
-  // times every kind on the caller's problem.
-  else if (want < 0 && !d->renumbered &&
-           (size_t)d->ld * sizeof(float) >= 8192 && 2 * (smem2 + 4096) <= (size_t)smem_optin) {
+  // automatic choice, measured on GB300 (FP32): on networks without node locality (random
+  // chords, n = 10^4, m = 10^5) the in-sum kind saves the node phase's second read of each F
+  // row (264 against 212 iterations/s for the register kind); on renumbered networks (kNN)
+  // the register kind's gathers hit L2, and the in-sum kind wins only on long rows (n = 10^4:
+  // 235 against 228/s; n = 3000: 1853 against 2672/s). mcf_autotune times every kind on the
+  // caller's problem.
+  else if (want < 0 &&
+           (size_t)d->ld * sizeof(float) >= (d->renumbered ? 32768u : 8192u) &&
+           2 * (smem2 + 4096) <= (size_t)smem_optin) {
     for (int c = 0; c < NUM_TMA && t < 0; ++c)
       if (kTmaVpt[c] * TMA_BLOCK >= nchunks) { t = c; kind = 2; }
   }
@@ -866,49 +955,65 @@ static int solve_t(mcf_problem* p, DeviceState* d, const mcf_options* o, mcf_res
 template <typename P, typename S>
 static int copy_outputs_t(mcf_problem* p, DeviceState* d, mcf_result* res, cudaStream_t st) {
   const int n = d->n, m = d->m;
-  const Topology& tp = p->topo;   // internal row node(j), column node(i) -> caller (i, j)
   const size_t ld = d->ld;
-  std::vector<P> buf;
-  if (res->T || res->Y) {
-    buf.resize((size_t)n * ld);
-    if (res->T) {
-      CK(cudaMemcpyAsync(buf.data(), d->That, buf.size() * sizeof(P), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j)
-          res->T[(size_t)i * n + j] = (double)buf[(size_t)tp.node(j) * ld + tp.node(i)];
-    }
-    if (res->Y) {
-      CK(cudaMemcpyAsync(buf.data(), d->Yhat, buf.size() * sizeof(P), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j)
-          res->Y[(size_t)i * n + j] = (double)buf[(size_t)tp.node(j) * ld + tp.node(i)];
-    }
-  }
-  if (res->F) {
-    P* tmp = nullptr;
-    if (cudaMalloc((void**)&tmp, (size_t)m * ld * sizeof(P)) != cudaSuccess) {
+  int rc = ensure_node_map(p, d, st);
+  if (rc != MCF_OK) return rc;
+  // out[r][c] = in[rowmap[c]][colmap[r]] in chunks of rows, through a device stage
+  auto gather = [&](const P* in, const int32_t* rowmap, int nrows, int ncols, double* out) -> int {
+    const int rows = chunk_rows(nrows, ncols);
+    double* stage = nullptr;
+    if (cudaMalloc((void**)&stage, (size_t)rows * ncols * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
+      set_error("device allocation for an output failed");
+      return MCF_ERR_OOM;
+    }
+    cudaError_t e = cudaSuccess;
+    for (int r0 = 0; r0 < nrows && e == cudaSuccess; r0 += rows) {
+      const int nr = std::min(rows, nrows - r0);
+      const dim3 grid((ncols + 31) / 32, (nr + 31) / 32);
+      gather_out_kernel<P><<<grid, dim3(32, 8), 0, st>>>(in, ld, rowmap, d->node_map, stage, r0,
+                                                         nr, ncols);
+      e = cudaGetLastError();
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out + (size_t)r0 * ncols, stage, (size_t)nr * ncols * sizeof(double),
+                            cudaMemcpyDeviceToHost, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(stage);
+    CK(e);
+    return MCF_OK;
+  };
+  // T[i][j] = That[node(j)][node(i)], Y likewise: row map node, column map node
+  if (res->T && (rc = gather((const P*)d->That, d->node_map, n, n, res->T)) != MCF_OK) return rc;
+  if (res->Y && (rc = gather((const P*)d->Yhat, d->node_map, n, n, res->Y)) != MCF_OK) return rc;
+  if (res->F) {
+    // F[i][l] = F^[internal edge of l][node(i)]
+    P* tmp = nullptr;
+    int32_t* emap = nullptr;
+    if (cudaMalloc((void**)&tmp, (size_t)m * ld * sizeof(P)) != cudaSuccess ||
+        cudaMalloc((void**)&emap, (size_t)m * 4) != cudaSuccess) {
+      cudaGetLastError();
+      if (tmp) cudaFree(tmp);
       set_error("device allocation for the F output failed");
       return MCF_ERR_OOM;
     }
+    std::vector<int32_t> inv(m);
+    for (int e2 = 0; e2 < m; ++e2) inv[p->topo.perm[e2]] = e2;
+    cudaError_t e = cudaMemcpyAsync(emap, inv.data(), (size_t)m * 4, cudaMemcpyHostToDevice, st);
     const int prev = d->cur ^ 1;   // F^{k-3/2} and Y^{k-1} of the last iteration
-    fhat_kernel<P, S><<<2048, 256, 0, st>>>((const S*)d->F[prev], (const P*)d->Y[prev],
-                                           d->lo_live ? (const __nv_bfloat16*)d->Ylo[prev] : nullptr,
-                                           d->e_tail, d->e_head, (const P*)d->mu,
-                                           (const P*)d->mu + m, d->sc, tmp, m,
-                                           (int)ld);
-    buf.resize((size_t)m * ld);
-    cudaError_t e = cudaMemcpyAsync(buf.data(), tmp, buf.size() * sizeof(P), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(tmp);
-    CK(e);
-    const std::vector<int32_t>& perm = p->topo.perm;
-    for (int e2 = 0; e2 < m; ++e2) {
-      const int l = perm[e2];
-      for (int i = 0; i < n; ++i) res->F[(size_t)i * m + l] = (double)buf[(size_t)e2 * ld + tp.node(i)];
+    if (e == cudaSuccess) {
+      fhat_kernel<P, S><<<2048, 256, 0, st>>>((const S*)d->F[prev], (const P*)d->Y[prev],
+                                             d->lo_live ? (const __nv_bfloat16*)d->Ylo[prev] : nullptr,
+                                             d->e_tail, d->e_head, (const P*)d->mu,
+                                             (const P*)d->mu + m, d->sc, tmp, m, (int)ld);
+      e = cudaGetLastError();
     }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // inv dies at return
+    rc = e == cudaSuccess ? gather(tmp, emap, n, m, res->F) : MCF_ERR_CUDA;
+    if (e != cudaSuccess) set_error(std::string("CUDA error ") + cudaGetErrorString(e));
+    cudaFree(tmp);
+    cudaFree(emap);
+    if (rc != MCF_OK) return rc;
   }
   return MCF_OK;
 }
