@@ -131,8 +131,13 @@ batch_edge_kernel(const BatchInst* __restrict__ insts, BatchClassDev cls) {
           for (int u = 0; u < VW; ++u) dl[u] = l1[u] - l2[u];
         }
 #pragma unroll
-        for (int u = 0; u < VW; ++u)
-          q[v][u] = shifted_q<P>(f[v][u], a1[u], a2[u], dl[u], alpha, mu0, mu0l);
+        for (int u = 0; u < VW; u += 2) {   // packed pairs, the same rounding as shifted_q
+          const float2 qq = shifted_q2(make_float2(f[v][u], f[v][u + 1]),
+                                       make_float2(a1[u], a1[u + 1]), make_float2(a2[u], a2[u + 1]),
+                                       make_float2(dl[u], dl[u + 1]), p2(alpha), p2(-mu0), p2(-mu0l));
+          q[v][u] = qq.x;
+          q[v][u + 1] = qq.y;
+        }
       } else {
 #pragma unroll
         for (int u = 0; u < VW; ++u) { f[v][u] = P(0); q[v][u] = shifted_floor<P>(mu0, mu0l); }
@@ -146,13 +151,18 @@ batch_edge_kernel(const BatchInst* __restrict__ insts, BatchClassDev cls) {
       const int ci = v * GROUP + lane;
       if (ci < nchunks) {
         P out[VW];
+        float2 sq = p2(0.f);   // (f^ - f)^2, the step itself (not the rounded difference)
 #pragma unroll
-        for (int u = 0; u < VW; ++u) {
-          const P fh = q[v][u] > mu ? q[v][u] - mu : P(0);
-          out[u] = rho * fh + (P(1) - rho) * f[v][u];
-          const P d = rho * (fh - f[v][u]);   // the step itself, not the rounded difference
-          dloc = fma(d, d, dloc);
+        for (int u = 0; u < VW; u += 2) {
+          const float2 ff = make_float2(f[v][u], f[v][u + 1]);
+          const float2 t2 = p2_add(make_float2(q[v][u], q[v][u + 1]), p2(-mu));
+          const float2 st = p2_sub(make_float2(fmaxf(t2.x, 0.f), fmaxf(t2.y, 0.f)), ff);
+          const float2 fnew = p2_fma(p2(rho), st, ff);   // rho f^ + (1 - rho) f
+          sq = p2_fma(st, st, sq);
+          out[u] = fnew.x;
+          out[u + 1] = fnew.y;
         }
+        dloc += rho * rho * (sq.x + sq.y);
         st_plain<P, VW>(fn + ci * VW, out);
       }
     }

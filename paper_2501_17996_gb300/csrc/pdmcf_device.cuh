@@ -1016,6 +1016,21 @@ node_kernel(IterArgs<P, S> a) {
       for (int u = 0; u < VW; ++u) s[u] = P(0);
       if (pin_rows) ld_plain<P, VW>(a.Pin + (size_t)j * a.ld + ci * VW, s);
       int k = 0;
+      if constexpr (sizeof(S) == 2 && VW == 4) {
+        // 8-byte BF16 words: eight rows in flight keep as many bytes in flight as four FP32
+        // rows; the rows are added in the same pairs and order as below
+        for (; k + 7 < deg; k += 8) {
+          S fr[8][VW];
+#pragma unroll
+          for (int r = 0; r < 8; ++r) ld_plain<S, VW>(row(k + r) + ci * VW, fr[r]);
+#pragma unroll
+          for (int r = 0; r < 8; r += 2) {
+            const P sa = k + r < nin ? P(1) : P(-1), sb = k + r + 1 < nin ? P(1) : P(-1);
+#pragma unroll
+            for (int u = 0; u < VW; ++u) s[u] += sa * to_p<P>(fr[r][u]) + sb * to_p<P>(fr[r + 1][u]);
+          }
+        }
+      }
       for (; k + 3 < deg; k += 4) {
         const S* r0 = row(k);
         const S* r1 = row(k + 1);
