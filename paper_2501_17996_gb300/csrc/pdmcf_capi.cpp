@@ -156,16 +156,33 @@ static void build_topology(int n, const std::vector<int32_t>& tail_in,
   }
 }
 
-static int check_weights(int n, const double* w) {
-  if (!w) return fail(MCF_ERR_INVALID, "w is NULL");
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) {
-      if (i == j) continue;
-      const double x = w[(size_t)i * n + j];
-      if (!(x > 0.0) || !std::isfinite(x))
-        return fail(MCF_ERR_INVALID, "weights must be finite and > 0 off the diagonal");
+// Copies the n x n matrix src into dst, checking ok(x) on every off-diagonal entry; on a
+// failing entry returns MCF_ERR_INVALID with msg (dst is then unspecified).
+template <typename Ok>
+static int copy_matrix(int n, const double* src, pdmcf::HostMatrix& dst, Ok ok, const char* msg) {
+  dst.resize((size_t)n * n);
+  std::atomic<bool> bad{false};
+  double* out = dst.data();
+  pdmcf::parallel_ranges(n, (size_t)n * sizeof(double), [&](int64_t r0, int64_t r1) {
+    for (int i = (int)r0; i < (int)r1; ++i) {
+      const double* a = src + (size_t)i * n;
+      double* b = out + (size_t)i * n;
+      bool rok = true;
+      for (int j = 0; j < n; ++j) {
+        const double x = a[j];
+        b[j] = x;
+        if (j != i && !ok(x)) rok = false;
+      }
+      if (!rok) { bad.store(true, std::memory_order_relaxed); return; }
     }
-  return MCF_OK;
+  });
+  return bad.load() ? fail(MCF_ERR_INVALID, msg) : MCF_OK;
+}
+
+static int copy_weights(int n, const double* w, pdmcf::HostMatrix& dst) {
+  if (!w) return fail(MCF_ERR_INVALID, "w is NULL");
+  return copy_matrix(n, w, dst, [](double x) { return x > 0.0 && std::isfinite(x); },
+                     "weights must be finite and > 0 off the diagonal");
 }
 
 static int check_caps(int m, const double* cap) {
@@ -261,10 +278,11 @@ int mcf_create_problem(int32_t n, int32_t m, const int32_t* tail, const int32_t*
     return fail(MCF_ERR_INVALID, "duplicate (tail, head) edge");
   int rc = check_caps(m, cap);
   if (rc != MCF_OK) return rc;
-  rc = check_weights(n, w);
+  pdmcf::HostMatrix wcopy;
+  rc = copy_weights(n, w, wcopy);
   if (rc != MCF_OK) return rc;
   double gscalar = 0.5;
-  std::vector<double> gmat;
+  pdmcf::HostMatrix gmat;
   if (utility_kind == MCF_POW) {
     if (!gamma || (gamma_len != 1 && gamma_len != (int64_t)n * n))
       return fail(MCF_ERR_INVALID, "power utility needs gamma of length 1 or n*n");
@@ -272,11 +290,9 @@ int mcf_create_problem(int32_t n, int32_t m, const int32_t* tail, const int32_t*
       gscalar = gamma[0];
       if (!(gscalar > 0.0 && gscalar < 1.0)) return fail(MCF_ERR_INVALID, "gamma must be in (0, 1)");
     } else {
-      gmat.assign(gamma, gamma + (size_t)n * n);
-      for (int i = 0; i < n; ++i)
-        for (int j = 0; j < n; ++j)
-          if (i != j && !(gmat[(size_t)i * n + j] > 0.0 && gmat[(size_t)i * n + j] < 1.0))
-            return fail(MCF_ERR_INVALID, "gamma must be in (0, 1)");
+      rc = copy_matrix(n, gamma, gmat, [](double x) { return x > 0.0 && x < 1.0; },
+                       "gamma must be in (0, 1)");
+      if (rc != MCF_OK) return rc;
     }
   }
   if (!strongly_connected(n, t, h))
@@ -288,7 +304,7 @@ int mcf_create_problem(int32_t n, int32_t m, const int32_t* tail, const int32_t*
   p->tail = std::move(t);
   p->head = std::move(h);
   p->cap.assign(cap, cap + m);
-  p->w.assign(w, w + (size_t)n * n);
+  p->w = std::move(wcopy);
   p->gamma_scalar = gscalar;
   p->gamma_mat = std::move(gmat);
   build_topology(n, p->tail, p->head, p->topo);
@@ -311,10 +327,11 @@ int mcf_update_capacities(mcf_problem* p, const double* cap) {
 int mcf_update_weights(mcf_problem* p, const double* w) {
   if (!p) return fail(MCF_ERR_INVALID, "problem is NULL");
   if (p->busy.load() > 0) return fail(MCF_ERR_BUSY, kOutstanding);
-  int rc = check_weights(p->n, w);
+  pdmcf::HostMatrix wcopy;
+  int rc = copy_weights(p->n, w, wcopy);
   if (rc != MCF_OK) return rc;
   std::lock_guard<std::mutex> g(p->lock);
-  p->w.assign(w, w + (size_t)p->n * p->n);
+  p->w.swap(wcopy);
   p->data_dirty = true;
   return MCF_OK;
 }

@@ -4,8 +4,12 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <memory>
 #include <mutex>
+#include <algorithm>
 #include <string>
+#include <thread>
+#include <utility>
 #include <vector>
 
 #include "pdmcf.h"
@@ -31,6 +35,58 @@ struct Topology {
   int node(int caller) const { return node_of.empty() ? caller : node_of[caller]; }
 };
 
+// Allocator whose value-less construct() leaves doubles uninitialised, so resizing a host
+// copy of an n x n matrix does not write (and page in) every page on one thread before the
+// parallel copy does.
+template <typename T>
+struct DefaultInitAlloc : std::allocator<T> {
+  template <typename U> struct rebind { using other = DefaultInitAlloc<U>; };
+  DefaultInitAlloc() = default;
+  template <typename U> DefaultInitAlloc(const DefaultInitAlloc<U>&) noexcept {}
+  template <typename U> void construct(U* q) noexcept { ::new ((void*)q) U; }
+  template <typename U, typename... A> void construct(U* q, A&&... a) {
+    ::new ((void*)q) U(std::forward<A>(a)...);
+  }
+};
+using HostMatrix = std::vector<double, DefaultInitAlloc<double>>;
+
+// Runs fn(u0, u1) over ranges of [0, units) on up to 16 host threads when the work covers
+// at least 32 MB (unit_bytes per unit), else on the calling thread. Host passes over n x n
+// matrices (validation, copies, the first touch of fresh pages) scale with the cores; a
+// range whose thread cannot be started runs on the calling thread.
+template <typename Fn>
+inline void parallel_ranges(int64_t units, size_t unit_bytes, Fn fn) {
+  int64_t nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  if ((double)units * (double)unit_bytes < (double)(32u << 20)) nt = 1;
+  nt = std::min<int64_t>(nt, std::max<int64_t>(units, 1));
+  std::vector<std::thread> th;
+  for (int64_t k = 1; k < nt; ++k) {
+    const int64_t u0 = units * k / nt, u1 = units * (k + 1) / nt;
+    try {
+      th.emplace_back(fn, u0, u1);
+    } catch (...) {
+      fn(u0, u1);
+    }
+  }
+  fn((int64_t)0, units / nt);
+  for (auto& t : th) t.join();
+}
+
+// Writes one zero per 4 KB into [p, p + bytes) on parallel threads, so that a fresh output
+// buffer's pages are mapped (and zeroed by the system) in parallel rather than during a
+// single-threaded device-to-host copy. The contents are then overwritten.
+inline void prefault_host(void* p, size_t bytes) {
+  if (!p || bytes == 0) return;
+  constexpr size_t kPage = 4096;
+  unsigned char* b = static_cast<unsigned char*>(p);
+  parallel_ranges((int64_t)((bytes + kPage - 1) / kPage), kPage, [b, bytes](int64_t q0, int64_t q1) {
+    for (int64_t q = q0; q < q1; ++q) {
+      const size_t off = (size_t)q * kPage;
+      if (off < bytes) reinterpret_cast<volatile unsigned char*>(b)[off] = 0;
+    }
+  });
+}
+
 }  // namespace pdmcf
 
 struct mcf_problem {
@@ -38,9 +94,9 @@ struct mcf_problem {
   int kind = MCF_LOG;
   std::vector<int32_t> tail, head;     // caller order
   std::vector<double> cap;             // caller order
-  std::vector<double> w;               // n*n, w[i*n+j]
+  pdmcf::HostMatrix w;                 // n*n, w[i*n+j]
   double gamma_scalar = 0.5;
-  std::vector<double> gamma_mat;       // n*n or empty
+  pdmcf::HostMatrix gamma_mat;         // n*n or empty
   pdmcf::Topology topo;
   double eta = 0.0;
   double omega = 1.0;                  // resident primal weight (warm start)

@@ -983,6 +983,9 @@ static int copy_outputs_t(mcf_problem* p, DeviceState* d, mcf_result* res, cudaS
     CK(e);
     return MCF_OK;
   };
+  prefault_host(res->T, (size_t)n * n * sizeof(double));
+  prefault_host(res->Y, (size_t)n * n * sizeof(double));
+  prefault_host(res->F, (size_t)n * m * sizeof(double));
   // T[i][j] = That[node(j)][node(i)], Y likewise: row map node, column map node
   if (res->T && (rc = gather((const P*)d->That, d->node_map, n, n, res->T)) != MCF_OK) return rc;
   if (res->Y && (rc = gather((const P*)d->Yhat, d->node_map, n, n, res->Y)) != MCF_OK) return rc;

@@ -81,6 +81,38 @@ def test_invalid_problems_are_rejected(lib, case, code):
     assert lib.mcf_last_error() != ""
 
 
+def test_gamma_matrix_checked_off_the_diagonal_only(lib):
+    n, t, h, c = 3, [0, 1, 2], [1, 2, 0], [1.0, 1.0, 1.0]
+    g = np.full((n, n), 0.5)
+    g[0, 0] = 7.0                                   # diagonal entries are not used
+    lib.mcf_destroy_problem(_create(lib, n, t, h, c, kind="pow", gamma=g))
+    g[2, 1] = 1.0
+    with pytest.raises(lib.MCFError) as ei:
+        _create(lib, n, t, h, c, kind="pow", gamma=g)
+    assert ei.value.code == lib.MCF_ERR_INVALID and "gamma" in lib.mcf_last_error()
+
+
+@pytest.mark.parametrize("row", [0, 1049, 2099])
+def test_large_weight_matrix_checked_in_every_row(lib, row):
+    """n = 2100 (35 MB of weights: the multi-threaded copy); one bad entry in any row is
+    found, by creation and by an update, and a rejected update leaves the problem usable."""
+    n = 2100
+    t = np.arange(n, dtype=np.int32)
+    h = ((t + 1) % n).astype(np.int32)
+    c = np.ones(n)
+    w = np.ones((n, n))
+    bad = w.copy()
+    bad[row, (row + 7) % n] = -1.0
+    with pytest.raises(lib.MCFError) as ei:
+        _create(lib, n, t, h, c, w=bad)
+    assert ei.value.code == lib.MCF_ERR_INVALID
+    with lib.Problem(I.Instance(n, t, h, c, "log", w, None, "ring2100")) as p:
+        with pytest.raises(lib.MCFError) as ei:
+            p.update_weights(bad)
+        assert ei.value.code == lib.MCF_ERR_INVALID
+        p.update_weights(w * 2.0)
+
+
 def test_valid_problem_and_footprint(lib):
     inst = I.mid(0)
     with lib.Problem(inst) as p:
