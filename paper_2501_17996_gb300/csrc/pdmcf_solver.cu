@@ -428,19 +428,38 @@ static int configure_shape(DeviceState* d, int want) {
   return rc;
 }
 
-// Head-aligned split of the edge range into grid_tma contiguous pieces of about m/grid
-// edges (edges are sorted by head, so a head's in-edges never straddle two CTAs).
+// Head-aligned split of the edge range into at most grid_tma contiguous pieces (edges are
+// sorted by head, so a head's in-edges never straddle two CTAs). All CTAs are resident at
+// once and the phase ends with the longest piece, so the split minimises the longest one:
+// the smallest cap L for which greedy packing of whole heads into pieces of at most L edges
+// needs no more than grid_tma pieces (binary search on L; on the n = 10^4, m = 10^5 network
+// this gives 1.01 times the mean piece against 1.05 for cuts at multiples of m/grid).
 static int upload_cta_ranges(mcf_problem* p, DeviceState* d, cudaStream_t st) {
   if (d->tma < 0) return MCF_OK;
   const int G = d->grid_tma, n = d->n, m = d->m;
+  const std::vector<int32_t>& inp = p->topo.in_ptr;
+  auto pack = [&](int64_t L, std::vector<int32_t>* ptr) -> int64_t {
+    int64_t pieces = 0, cur = 0;
+    for (int j = 0; j < n; ++j) {
+      const int64_t deg = inp[j + 1] - inp[j];
+      if (cur > 0 && cur + deg > L) {
+        if (ptr && pieces + 1 <= G) (*ptr)[pieces + 1] = inp[j];
+        ++pieces;
+        cur = 0;
+      }
+      cur += deg;
+    }
+    return pieces + (cur > 0 ? 1 : 0);
+  };
+  int64_t lo = (m + G - 1) / G, hi = m;
+  for (int j = 0; j < n; ++j) lo = std::max<int64_t>(lo, inp[j + 1] - inp[j]);
+  while (lo < hi) {
+    const int64_t mid = lo + (hi - lo) / 2;
+    if (pack(mid, nullptr) <= G) hi = mid; else lo = mid + 1;
+  }
   std::vector<int32_t> ptr(G + 1, m);
   ptr[0] = 0;
-  int k = 1;
-  const std::vector<int32_t>& inp = p->topo.in_ptr;
-  for (int j = 0; j < n && k < G; ++j) {
-    const int end = inp[j + 1];
-    if ((long long)end * G >= (long long)k * m) ptr[k++] = end;
-  }
+  pack(lo, &ptr);
   if (d->cta_ptr) cudaFree(d->cta_ptr);
   d->cta_ptr = nullptr;
   if (cudaMalloc((void**)&d->cta_ptr, (G + 1) * sizeof(int32_t)) != cudaSuccess) {
