@@ -18,6 +18,8 @@ namespace pdmcf {
 struct DeviceState;   // defined in pdmcf_solver.cu
 
 void set_error(const std::string& msg);   // thread-local message for mcf_last_error()
+// Unique id of the calling thread's current CUDA context, 0 if none (pdmcf_noalloc.cu).
+unsigned long long current_context_id();
 
 // Internal edge order: edges sorted by head, so each node's in-edges are one contiguous
 // range of rows of F; out-edges are listed through out_ptr/out_idx.

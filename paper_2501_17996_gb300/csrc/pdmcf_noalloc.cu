@@ -22,23 +22,6 @@ int project_validate(int32_t n, int32_t m, int32_t ld, const float* Qt, const fl
                      const float* Ft, const float* mu);
 int project_launch(int32_t n, int32_t m, int32_t ld, const float* Qt, const float* cap,
                    float* Ft, float* mu, double* dist2, cudaStream_t st, double* scratch);
-}  // namespace pdmcf
-
-// Largest column count the fixed scratch serves: 262144 columns, 2 MiB of doubles.
-#define MCF_NOALLOC_MAX_COLS (1 << 18)
-
-// Per-column squared distances [0, m) and their fixed-order total [m]. Each call writes
-// every entry it reads, so nothing has to be cleared between calls.
-static __device__ __align__(256) double g_noalloc_scratch[MCF_NOALLOC_MAX_COLS + 1];
-
-namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-struct ScratchAddr {
-  unsigned long long ctx_id = 0;   // context the address belongs to (0: not looked up)
-  double* addr = nullptr;
-};
-ScratchAddr g_scratch[kMaxDevices];
 
 using CtxGetCurrentFn = CUresult (*)(CUcontext*);
 using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
@@ -67,6 +50,23 @@ unsigned long long current_context_id() {
   if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
   return id;
 }
+}  // namespace pdmcf
+
+// Largest column count the fixed scratch serves: 262144 columns, 2 MiB of doubles.
+#define MCF_NOALLOC_MAX_COLS (1 << 18)
+
+// Per-column squared distances [0, m) and their fixed-order total [m]. Each call writes
+// every entry it reads, so nothing has to be cleared between calls.
+static __device__ __align__(256) double g_noalloc_scratch[MCF_NOALLOC_MAX_COLS + 1];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+struct ScratchAddr {
+  unsigned long long ctx_id = 0;   // context the address belongs to (0: not looked up)
+  double* addr = nullptr;
+};
+ScratchAddr g_scratch[kMaxDevices];
 
 // Device address of the scratch array in the current device's context. In host code the
 // array's name is only a host-side stand-in, so kernels must be given this address. It is
@@ -86,7 +86,7 @@ int scratch_address(double** out) {
   }
   std::lock_guard<std::mutex> g(g_mu);
   ScratchAddr& s = g_scratch[dev];
-  const unsigned long long ctx = current_context_id();
+  const unsigned long long ctx = pdmcf::current_context_id();
   if (!s.addr || ctx == 0 || ctx != s.ctx_id) {
     double* p = nullptr;
     e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
@@ -96,7 +96,7 @@ int scratch_address(double** out) {
       return MCF_ERR_CUDA;
     }
     s.addr = p;
-    s.ctx_id = current_context_id();   // the lookup makes the primary context current
+    s.ctx_id = pdmcf::current_context_id();   // the lookup makes the primary context current
   }
   *out = s.addr;
   return MCF_OK;

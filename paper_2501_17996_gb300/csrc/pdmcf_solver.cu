@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <limits>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -120,6 +121,7 @@ struct DeviceState {
   DevScalars* sc = nullptr;
   DevScalars* sc_host = nullptr;
   cudaStream_t own_stream = nullptr;
+  cudaMemPool_t pool = nullptr;   // where the buffers below come from (nullptr: cudaMalloc)
   int shape = -1, auto_shape = -1, block = 0, grid_edge = 0, grid_node = 0, grid_check = 0;
   int requested_shape = -1;   // mcf_options.shape the grids were configured for
   // pipelined edge phase (tma >= 0): one CTA per SM over head-aligned edge ranges
@@ -171,16 +173,113 @@ static void destroy_graphs(DeviceState* d) {
   d->graph_len = 0;
 }
 
+// ------------------------------------------------------------------ device memory
+// A problem's device state (about 11 GB at n = 10^4, m = 10^5) and the boundary's staging
+// buffers come from one stream-ordered memory pool per device, which keeps up to 32 GB of
+// freed memory for reuse: releasing a state with cudaFree took 12 ms at that size, and every
+// cold solve of a new network paid it and the allocations again. The pool is created again
+// when the device's context has changed (a cudaDeviceReset by the application); a device
+// without memory pools uses cudaMalloc/cudaFree.
+namespace {
+struct PoolSlot {
+  cudaMemPool_t pool = nullptr;
+  unsigned long long ctx = 0;
+  bool unsupported = false;
+};
+constexpr int kPoolDevices = 64;
+std::mutex g_pool_mu;
+PoolSlot g_pools[kPoolDevices];
+}  // namespace
+
+static cudaMemPool_t state_pool(int device) {
+  if (device < 0 || device >= kPoolDevices) return nullptr;
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  PoolSlot& s = g_pools[device];
+  if (s.unsupported) return nullptr;
+  const unsigned long long ctx = current_context_id();
+  if (s.pool && (ctx == 0 || ctx == s.ctx)) return s.pool;
+  int ok = 0;
+  if (cudaDeviceGetAttribute(&ok, cudaDevAttrMemoryPoolsSupported, device) != cudaSuccess || !ok) {
+    cudaGetLastError();
+    s.unsupported = true;
+    return nullptr;
+  }
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = device;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+    cudaGetLastError();
+    s.unsupported = true;
+    return nullptr;
+  }
+  uint64_t keep = (uint64_t)32 << 30;
+  cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  s.pool = pool;
+  s.ctx = ctx;
+  return pool;
+}
+
+// A buffer of the state, ready for use on any stream when this returns.
+static bool dalloc(DeviceState* d, void** p, size_t bytes) {
+  *p = nullptr;
+  cudaError_t e;
+  if (d->pool) {
+    e = cudaMallocFromPoolAsync(p, bytes, d->pool, d->own_stream);
+    if (e == cudaErrorMemoryAllocation) {   // return the pool's cached memory and retry
+      cudaGetLastError();
+      cudaStreamSynchronize(d->own_stream);
+      cudaMemPoolTrimTo(d->pool, 0);
+      e = cudaMallocFromPoolAsync(p, bytes, d->pool, d->own_stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d->own_stream);
+  } else {
+    e = cudaMalloc(p, bytes);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return false;
+  }
+  return true;
+}
+
+// Frees a state buffer; the caller has made sure no device work still uses it (as cudaFree
+// does by synchronizing the device).
+static void dfree(DeviceState* d, void* p) {
+  if (!p) return;
+  if (d->pool) cudaFreeAsync(p, d->own_stream);
+  else cudaFree(p);
+}
+
+// A staging buffer used on stream st only: allocated, used and freed in st's order.
+static bool salloc(DeviceState* d, void** p, size_t bytes, cudaStream_t st) {
+  *p = nullptr;
+  const cudaError_t e = d->pool ? cudaMallocFromPoolAsync(p, bytes, d->pool, st) : cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return false;
+  }
+  return true;
+}
+static void sfree(DeviceState* d, void* p, cudaStream_t st) {
+  if (!p) return;
+  if (d->pool) cudaFreeAsync(p, st);
+  else cudaFree(p);
+}
+
 static void free_state(DeviceState* d) {
   if (!d) return;
   cudaSetDevice(d->device);
   destroy_graphs(d);
+  cudaDeviceSynchronize();   // no kernel or copy may still use the buffers
   void* bufs[] = {d->F[0], d->F[1], d->Y[0], d->Y[1], d->Ylo[0], d->Ylo[1], d->Pm, d->W, d->G, d->mu, d->cap,
                   d->That, d->Uprime, d->Yhat, d->e_tail, d->e_head, d->in_ptr,
                   d->out_ptr, d->out_idx, d->part_edge, d->part_node, d->part_check, d->sc,
                   d->Pin, d->cta_ptr, d->node_map};
-  for (void* b : bufs)
-    if (b) cudaFree(b);
+  for (void* b : bufs) dfree(d, b);
   if (d->sc_host) cudaFreeHost(d->sc_host);
   if (d->own_stream) cudaStreamDestroy(d->own_stream);
   delete d;
@@ -261,8 +360,7 @@ static int ensure_node_map(mcf_problem* p, DeviceState* d, cudaStream_t st) {
   if (d->node_map) return MCF_OK;
   std::vector<int32_t> nm(d->n);
   for (int i = 0; i < d->n; ++i) nm[i] = p->topo.node(i);
-  if (cudaMalloc((void**)&d->node_map, (size_t)d->n * 4) != cudaSuccess) {
-    cudaGetLastError();
+  if (!dalloc(d, (void**)&d->node_map, (size_t)d->n * 4)) {
     set_error("device allocation failed");
     return MCF_ERR_OOM;
   }
@@ -289,8 +387,7 @@ static int upload_data(mcf_problem* p, DeviceState* d, cudaStream_t st) {
   if (rc != MCF_OK) return rc;
   const int rows = chunk_rows(n, n);
   double* stage = nullptr;
-  if (cudaMalloc((void**)&stage, (size_t)rows * n * sizeof(double)) != cudaSuccess) {
-    cudaGetLastError();
+  if (!salloc(d, (void**)&stage, (size_t)rows * n * sizeof(double), st)) {
     set_error("device allocation for the weight upload failed");
     return MCF_ERR_OOM;
   }
@@ -311,7 +408,7 @@ static int upload_data(mcf_problem* p, DeviceState* d, cudaStream_t st) {
   cudaError_t e = place(p->w.data(), d->W, P(0));
   if (e == cudaSuccess && d->G) e = place(p->gamma_mat.data(), d->G, P(0.5));
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // the stage and the host vectors
-  cudaFree(stage);
+  sfree(d, stage, st);
   CK(e);
   p->data_dirty = false;
   return MCF_OK;
@@ -460,15 +557,16 @@ static int upload_cta_ranges(mcf_problem* p, DeviceState* d, cudaStream_t st) {
   std::vector<int32_t> ptr(G + 1, m);
   ptr[0] = 0;
   pack(lo, &ptr);
-  if (d->cta_ptr) cudaFree(d->cta_ptr);
+  if (d->cta_ptr) {
+    cudaDeviceSynchronize();
+    dfree(d, d->cta_ptr);
+  }
   d->cta_ptr = nullptr;
-  if (cudaMalloc((void**)&d->cta_ptr, (G + 1) * sizeof(int32_t)) != cudaSuccess) {
-    cudaGetLastError();
+  if (!dalloc(d, (void**)&d->cta_ptr, (G + 1) * sizeof(int32_t))) {
     set_error("device allocation failed");
     return MCF_ERR_OOM;
   }
-  if (!d->Pin && cudaMalloc(&d->Pin, (size_t)n * d->ld * sizeof(float)) != cudaSuccess) {
-    cudaGetLastError();
+  if (!d->Pin && !dalloc(d, &d->Pin, (size_t)n * d->ld * sizeof(float))) {
     set_error("device allocation failed");
     return MCF_ERR_OOM;
   }
@@ -479,13 +577,13 @@ static int upload_cta_ranges(mcf_problem* p, DeviceState* d, cudaStream_t st) {
 
 // (Re)allocate the per-block partial arrays for the current grids.
 static int alloc_partials(DeviceState* d) {
+  if (d->part_edge || d->part_node || d->part_check) cudaDeviceSynchronize();
   for (double** b : {&d->part_edge, &d->part_node, &d->part_check})
-    if (*b) { cudaFree(*b); *b = nullptr; }
-  bool ok = cudaMalloc((void**)&d->part_edge, (size_t)std::max({d->grid_edge, d->grid_tma, 1}) * sizeof(double)) == cudaSuccess &&
-            cudaMalloc((void**)&d->part_node, (size_t)std::max({d->grid_node, d->grid_node_pin, 1}) * NODE_PARTS * sizeof(double)) == cudaSuccess &&
-            cudaMalloc((void**)&d->part_check, (size_t)std::max(d->grid_check, 1) * CHECK_PARTS * sizeof(double)) == cudaSuccess;
+    if (*b) { dfree(d, *b); *b = nullptr; }
+  bool ok = dalloc(d, (void**)&d->part_edge, (size_t)std::max({d->grid_edge, d->grid_tma, 1}) * sizeof(double)) &&
+            dalloc(d, (void**)&d->part_node, (size_t)std::max({d->grid_node, d->grid_node_pin, 1}) * NODE_PARTS * sizeof(double)) &&
+            dalloc(d, (void**)&d->part_check, (size_t)std::max(d->grid_check, 1) * CHECK_PARTS * sizeof(double));
   if (!ok) {
-    cudaGetLastError();
     set_error("device allocation failed");
     return MCF_ERR_OOM;
   }
@@ -518,8 +616,30 @@ static int alloc_state(mcf_problem* p, int precision, int device, int shape, cud
   if (rc != MCF_OK) { free_state(d); return rc; }
   d->requested_shape = shape;
   const size_t n = d->n, m = d->m, ld = d->ld;
+  if (cudaStreamCreateWithFlags(&d->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    free_state(d);
+    set_error("stream creation failed");
+    return MCF_ERR_CUDA;
+  }
+  d->pool = state_pool(device);
+  // pooled allocations are ordered on own_stream; one synchronisation below makes them all
+  // usable from any stream
   auto A = [&](void** ptr, size_t bytes) -> bool {
-    if (cudaMalloc(ptr, bytes) != cudaSuccess) { cudaGetLastError(); return false; }
+    *ptr = nullptr;
+    cudaError_t ea;
+    if (d->pool) {
+      ea = cudaMallocFromPoolAsync(ptr, bytes, d->pool, d->own_stream);
+      if (ea == cudaErrorMemoryAllocation) {   // return the pool's cached memory and retry
+        cudaGetLastError();
+        cudaStreamSynchronize(d->own_stream);
+        cudaMemPoolTrimTo(d->pool, 0);
+        ea = cudaMallocFromPoolAsync(ptr, bytes, d->pool, d->own_stream);
+      }
+    } else {
+      ea = cudaMalloc(ptr, bytes);
+    }
+    if (ea != cudaSuccess) { cudaGetLastError(); *ptr = nullptr; return false; }
     return true;
   };
   bool ok = true;
@@ -532,21 +652,22 @@ static int alloc_state(mcf_problem* p, int precision, int device, int shape, cud
   ok = ok && A((void**)&d->e_tail, m * 4) && A((void**)&d->e_head, m * 4) &&
        A((void**)&d->in_ptr, (n + 1) * 4) && A((void**)&d->out_ptr, (n + 1) * 4) &&
        A((void**)&d->out_idx, m * 4);
-  ok = ok && A((void**)&d->sc, sizeof(DevScalars)) && alloc_partials(d) == MCF_OK;
+  ok = ok && A((void**)&d->sc, sizeof(DevScalars));
+  if (ok && d->pool && cudaStreamSynchronize(d->own_stream) != cudaSuccess) {
+    cudaGetLastError();
+    ok = false;
+  }
+  ok = ok && alloc_partials(d) == MCF_OK;
   if (!ok) {
     free_state(d);
     set_error("device allocation failed");
     return MCF_ERR_OOM;
   }
   if (cudaMallocHost((void**)&d->sc_host, sizeof(DevScalars)) != cudaSuccess) {
+    cudaGetLastError();
     free_state(d);
     set_error("pinned host allocation failed");
     return MCF_ERR_OOM;
-  }
-  if (cudaStreamCreateWithFlags(&d->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
-    free_state(d);
-    set_error("stream creation failed");
-    return MCF_ERR_CUDA;
   }
   cudaStream_t st = st_hint ? st_hint : d->own_stream;
   const Topology& t = p->topo;
@@ -981,8 +1102,7 @@ static int copy_outputs_t(mcf_problem* p, DeviceState* d, mcf_result* res, cudaS
   auto gather = [&](const P* in, const int32_t* rowmap, int nrows, int ncols, double* out) -> int {
     const int rows = chunk_rows(nrows, ncols);
     double* stage = nullptr;
-    if (cudaMalloc((void**)&stage, (size_t)rows * ncols * sizeof(double)) != cudaSuccess) {
-      cudaGetLastError();
+    if (!salloc(d, (void**)&stage, (size_t)rows * ncols * sizeof(double), st)) {
       set_error("device allocation for an output failed");
       return MCF_ERR_OOM;
     }
@@ -998,7 +1118,7 @@ static int copy_outputs_t(mcf_problem* p, DeviceState* d, mcf_result* res, cudaS
                             cudaMemcpyDeviceToHost, st);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(stage);
+    sfree(d, stage, st);
     CK(e);
     return MCF_OK;
   };
@@ -1012,10 +1132,9 @@ static int copy_outputs_t(mcf_problem* p, DeviceState* d, mcf_result* res, cudaS
     // F[i][l] = F^[internal edge of l][node(i)]
     P* tmp = nullptr;
     int32_t* emap = nullptr;
-    if (cudaMalloc((void**)&tmp, (size_t)m * ld * sizeof(P)) != cudaSuccess ||
-        cudaMalloc((void**)&emap, (size_t)m * 4) != cudaSuccess) {
-      cudaGetLastError();
-      if (tmp) cudaFree(tmp);
+    if (!salloc(d, (void**)&tmp, (size_t)m * ld * sizeof(P), st) ||
+        !salloc(d, (void**)&emap, (size_t)m * 4, st)) {
+      sfree(d, tmp, st);
       set_error("device allocation for the F output failed");
       return MCF_ERR_OOM;
     }
@@ -1033,8 +1152,8 @@ static int copy_outputs_t(mcf_problem* p, DeviceState* d, mcf_result* res, cudaS
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // inv dies at return
     rc = e == cudaSuccess ? gather(tmp, emap, n, m, res->F) : MCF_ERR_CUDA;
     if (e != cudaSuccess) set_error(std::string("CUDA error ") + cudaGetErrorString(e));
-    cudaFree(tmp);
-    cudaFree(emap);
+    sfree(d, tmp, st);
+    sfree(d, emap, st);
     if (rc != MCF_OK) return rc;
   }
   return MCF_OK;
