@@ -170,7 +170,9 @@ int mcf_update_capacities(mcf_problem* p, const double* cap);
 int mcf_update_weights(mcf_problem* p, const double* w);
 
 /* Free the problem and its device memory. Must not be called while a ticket on it is
- * pending. NULL is accepted. */
+ * pending. NULL is accepted. The device memory goes back to the library's stream-ordered
+ * pool for that device, which keeps up to 32 GB of freed memory for the next problem's
+ * state (and gives cached memory back when an allocation would otherwise fail). */
 int mcf_destroy_problem(mcf_problem* p);
 
 /* Size queries. */
