@@ -185,6 +185,40 @@ def test_slice_pipelined_shapes_fp32(lib):
             assert rel_err(g["Y"], ref.Yhat, m) < 1e-4, s
 
 
+def _hub_network(n=2000, seed=0):
+    """A ring in both directions plus edges from every other node to node 0 and back: node 0
+    has in-degree n - 1, so the head-aligned CTA ranges of kinds 1 and 2 hold the hub's in-edges
+    in one range and most CTAs get an empty range."""
+    rng = np.random.default_rng(seed)
+    i = np.arange(n)
+    j = np.arange(2, n - 1)              # ring neighbours of node 0 are linked already
+    zero = np.zeros(j.size, dtype=np.int64)
+    tail = np.concatenate([i, (i + 1) % n, j, zero])
+    head = np.concatenate([(i + 1) % n, i, zero, j])
+    cap = rng.lognormal(0.0, 0.5, size=tail.size)
+    w = rng.uniform(0.5, 1.5, size=(n, n))
+    np.fill_diagonal(w, 0.0)
+    return I.Instance(n, tail.astype(np.int32), head.astype(np.int32), cap, "pow", w, 0.5, "hub")
+
+
+def test_hub_network_pipelined_shapes_fp32(lib):
+    """Every bulk-copy pipelined and in-sum shape on a network with one node of in-degree
+    n + 1 (one long head group, empty CTA ranges) against the oracle."""
+    inst = _hub_network()
+    K = 6
+    ref = oracle_k(inst, K, 3)
+    m = off(inst.n)
+    piped = [s for s, (g, v, b, t) in enumerate(lib.mcf_shape_info())
+             if t and g * v >= ((inst.n + 7) // 8 * 8) // 4]
+    assert piped
+    with lib.Problem(inst) as p:
+        for s in piped:
+            g = p.solve(precision="fp32", stop_mode="none", max_iters=K, k_check=3, shape=s,
+                        want_T=True, want_Y=True)
+            assert rel_err(g["T"], ref.T, m) < 1e-4, s
+            assert rel_err(g["Y"], ref.Yhat, m) < 1e-4, s
+
+
 def test_bf16_storage_every_shape_short_trajectory(lib):
     """F stored as BF16 (8-bit mantissa) for every shape, 3 iterations: each stored F value
     is rounded, so the bound is 1e-2 of scale; indexing mistakes give O(1) errors."""
