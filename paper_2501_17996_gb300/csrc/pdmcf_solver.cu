@@ -221,6 +221,18 @@ static cudaMemPool_t state_pool(int device) {
   return pool;
 }
 
+// The kernels' vector loads and bulk copies need 16-byte aligned buffers (cudaMalloc returns
+// 256-byte aligned ones); a buffer that is not aligned is refused rather than used.
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Frees a state buffer; the caller has made sure no device work still uses it (as cudaFree
+// does by synchronizing the device).
+static void dfree(DeviceState* d, void* p) {
+  if (!p) return;
+  if (d->pool) cudaFreeAsync(p, d->own_stream);
+  else cudaFree(p);
+}
+
 // A buffer of the state, ready for use on any stream when this returns.
 static bool dalloc(DeviceState* d, void** p, size_t bytes) {
   *p = nullptr;
@@ -242,18 +254,20 @@ static bool dalloc(DeviceState* d, void** p, size_t bytes) {
     *p = nullptr;
     return false;
   }
+  if (!aligned16(*p)) {
+    dfree(d, *p);
+    *p = nullptr;
+    return false;
+  }
   return true;
 }
 
-// Frees a state buffer; the caller has made sure no device work still uses it (as cudaFree
-// does by synchronizing the device).
-static void dfree(DeviceState* d, void* p) {
+// A staging buffer used on stream st only: allocated, used and freed in st's order.
+static void sfree(DeviceState* d, void* p, cudaStream_t st) {
   if (!p) return;
-  if (d->pool) cudaFreeAsync(p, d->own_stream);
+  if (d->pool) cudaFreeAsync(p, st);
   else cudaFree(p);
 }
-
-// A staging buffer used on stream st only: allocated, used and freed in st's order.
 static bool salloc(DeviceState* d, void** p, size_t bytes, cudaStream_t st) {
   *p = nullptr;
   const cudaError_t e = d->pool ? cudaMallocFromPoolAsync(p, bytes, d->pool, st) : cudaMalloc(p, bytes);
@@ -262,12 +276,12 @@ static bool salloc(DeviceState* d, void** p, size_t bytes, cudaStream_t st) {
     *p = nullptr;
     return false;
   }
+  if (!aligned16(*p)) {
+    sfree(d, *p, st);
+    *p = nullptr;
+    return false;
+  }
   return true;
-}
-static void sfree(DeviceState* d, void* p, cudaStream_t st) {
-  if (!p) return;
-  if (d->pool) cudaFreeAsync(p, st);
-  else cudaFree(p);
 }
 
 static void free_state(DeviceState* d) {
@@ -640,6 +654,7 @@ static int alloc_state(mcf_problem* p, int precision, int device, int shape, cud
       ea = cudaMalloc(ptr, bytes);
     }
     if (ea != cudaSuccess) { cudaGetLastError(); *ptr = nullptr; return false; }
+    if (!aligned16(*ptr)) { dfree(d, *ptr); *ptr = nullptr; return false; }
     return true;
   };
   bool ok = true;
