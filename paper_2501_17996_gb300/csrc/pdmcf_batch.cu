@@ -289,7 +289,7 @@ int BatchEngine::upload_lists() {
   return MCF_OK;
 }
 
-int BatchEngine::launch_iteration(cudaStream_t st) {
+int BatchEngine::launch_iteration(cudaStream_t st, bool with_check) {
   const BatchTable& T = batch_table();
   const size_t S = max_slots_;
   for (int c = 0; c < NUM_SHAPES; ++c) {
@@ -301,7 +301,8 @@ int BatchEngine::launch_iteration(cudaStream_t st) {
     const int block = kShapes[c].block;
     BCK(cudaLaunchKernel((const void*)T.edge[c], dim3(grid_[0][c]), dim3(block), kargs, 0, st));
     BCK(cudaLaunchKernel((const void*)T.node[c], dim3(grid_[1][c]), dim3(block), kargs, 0, st));
-    BCK(cudaLaunchKernel((const void*)T.check[c], dim3(grid_[2][c]), dim3(block), kargs, 0, st));
+    if (with_check)
+      BCK(cudaLaunchKernel((const void*)T.check[c], dim3(grid_[2][c]), dim3(block), kargs, 0, st));
   }
   BatchScalarArgs sa{d_insts_, d_slot_list_, d_nslots_};
   batch_scalar_kernel<<<max_slots_, 256, 0, st>>>(sa);
@@ -321,6 +322,26 @@ int BatchEngine::step(int iters) {
   return rc;
 }
 
+// Iterations i of the next chunk (bit i) in which some active instance takes a stop test
+// (batch_is_check at its k = k0 + i): the check launch of the other iterations would find
+// nothing to do for any instance, so it is left out. Chunks longer than 64 iterations keep it
+// in every iteration.
+uint64_t BatchEngine::check_iterations(int iters) const {
+  if (iters > 64) return ~0ull;
+  uint64_t mask = 0;
+  for (int s = 0; s < max_slots_; ++s) {
+    const BatchSlot& sl = slots_[s];
+    const BatchScalars& h = h_sc_[s];
+    if (!sl.used || sl.finished || !h.active) continue;
+    const long long kc = std::max(1LL, h.k_check);
+    for (int i = 0; i < iters; ++i) {
+      const long long k1 = h.s.k + i + 1;
+      if (k1 % kc == 0 || k1 >= h.max_iters) mask |= 1ull << i;
+    }
+  }
+  return mask;
+}
+
 int BatchEngine::step_impl(int iters) {
   BCK(cudaSetDevice(device_));
   if (lists_dirty_) {
@@ -328,13 +349,16 @@ int BatchEngine::step_impl(int iters) {
     if (rc != MCF_OK) return rc;
   }
   if (class_mask_ == 0) return MCF_OK;
-  const auto key = std::make_pair(class_mask_, iters);
+  const uint64_t checks = check_iterations(iters);
+  auto with_check = [&](int i) { return i >= 64 || ((checks >> i) & 1ull) != 0; };
+  const auto key = std::make_tuple(class_mask_, iters, checks);
   auto it = graphs_.find(key);
   if (it == graphs_.end() && !graphs_broken_) {
+    if (graphs_.size() >= 64) destroy_graphs();   // bound the cache
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ge = nullptr;
     bool ok = cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-    for (int i = 0; i < iters && ok; ++i) ok = launch_iteration(stream_) == MCF_OK;
+    for (int i = 0; i < iters && ok; ++i) ok = launch_iteration(stream_, with_check(i)) == MCF_OK;
     const cudaError_t e = cudaStreamEndCapture(stream_, &g);
     ok = ok && e == cudaSuccess && g && cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
     if (g) cudaGraphDestroy(g);
@@ -349,7 +373,7 @@ int BatchEngine::step_impl(int iters) {
     BCK(cudaGraphLaunch(it->second, stream_));
   } else {
     for (int i = 0; i < iters; ++i) {
-      int rc = launch_iteration(stream_);
+      int rc = launch_iteration(stream_, with_check(i));
       if (rc != MCF_OK) return rc;
     }
   }

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <map>
+#include <tuple>
 #include <vector>
 
 #include "pdmcf_batch.cuh"
@@ -62,7 +63,8 @@ class BatchEngine {
  private:
   int step_impl(int iters);
   int upload_lists();
-  int launch_iteration(cudaStream_t st);
+  int launch_iteration(cudaStream_t st, bool with_check);
+  uint64_t check_iterations(int iters) const;
   void destroy_graphs();
 
   int device_;
@@ -83,7 +85,8 @@ class BatchEngine {
   std::vector<BatchInst> h_insts_;
   bool lists_dirty_ = true;
   unsigned class_mask_ = 0;
-  std::map<std::pair<unsigned, int>, cudaGraphExec_t> graphs_;
+  // key: class mask, iterations per chunk, iterations of the chunk with a stop test
+  std::map<std::tuple<unsigned, int, uint64_t>, cudaGraphExec_t> graphs_;
   bool graphs_broken_ = false;
   std::vector<int> finished_;
 };
