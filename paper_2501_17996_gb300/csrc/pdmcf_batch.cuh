@@ -214,8 +214,31 @@ batch_node_kernel(const BatchInst* __restrict__ insts, BatchClassDev cls) {
       for (int u = 0; u < VW; ++u) s[v][u] = P(0);
     const int ib = I.in_ptr[j], nin = I.in_ptr[j + 1] - ib;
     const int ob = I.out_ptr[j], deg = nin + (I.out_ptr[j + 1] - ob);
-    for (int k = 0; k < deg; ++k) {
-      const float* r = Fn + (size_t)(k < nin ? ib + k : I.out_idx[ob + k - nin]) * I.ld;
+    auto row = [&](int k) {
+      return Fn + (size_t)(k < nin ? ib + k : I.out_idx[ob + k - nin]) * I.ld;
+    };
+    // four edge rows in flight, summed in edge order (the same order as one at a time)
+    int k = 0;
+    for (; k + 4 <= deg; k += 4) {
+      const float* r[4] = {row(k), row(k + 1), row(k + 2), row(k + 3)};
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        const int ci = v * GROUP + lane;
+        if (ci < nchunks) {
+          P fr[4][VW];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) ld_plain<P, VW>(r[q] + ci * VW, fr[q]);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const P sg = k + q < nin ? P(1) : P(-1);
+#pragma unroll
+            for (int u = 0; u < VW; ++u) s[v][u] += sg * fr[q][u];
+          }
+        }
+      }
+    }
+    for (; k < deg; ++k) {
+      const float* r = row(k);
       const P sg = k < nin ? P(1) : P(-1);
 #pragma unroll
       for (int v = 0; v < VPT; ++v) {
