@@ -651,7 +651,7 @@ def run_served(args, rank, world, local_rank):
         "steps": served["completed"], "warmup": 1, "ms_per_step": None,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": "served: Poisson %.0f req/s for %.0f s, n in {100,300,1000,3000}, "
+        "config": {"workload": "served: Poisson %g req/s for %g s, n in {100,300,1000,3000}, "
                                "out-degree 8, 70%% warm (+-10%% c or w), 30%% cold, "
                                "rel_kkt < 1e-4, 120 GB budget" % (args.rate, args.window),
                    "networks": len(nets)},
