@@ -450,7 +450,8 @@ def run_ours(args, rank, world, local_rank):
                 "peak_gbs": peak, "kernels": per_kernel},
         "e2e": {"value": e2e_value, "unit": "iters/s", "h2d_bytes_per_step": h2d / args.steps,
                 "d2h_bytes_per_step": d2h / args.steps,
-                "note": "problem creation + upload, %d iterations, T read-back" % args.steps},
+                "note": ("problem creation + upload, %d iterations, T read-back (after the device-resident "
+                         "leg in the same process, so the device memory pool is warm)" % args.steps)},
         "gpu_launches": launches,
         "clocks": clk.summary(),
         "cold_start": cold,
