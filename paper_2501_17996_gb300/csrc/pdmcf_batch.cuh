@@ -207,50 +207,11 @@ batch_node_kernel(const BatchInst* __restrict__ insts, BatchClassDev cls) {
     const P inv_rho = P(1) / rho;
     const int nchunks = I.ld / VW;
     const float* Fn = I.F[par ^ 1];
-    P s[VPT][VW];
-#pragma unroll
-    for (int v = 0; v < VPT; ++v)
-#pragma unroll
-      for (int u = 0; u < VW; ++u) s[v][u] = P(0);
     const int ib = I.in_ptr[j], nin = I.in_ptr[j + 1] - ib;
     const int ob = I.out_ptr[j], deg = nin + (I.out_ptr[j + 1] - ob);
     auto row = [&](int k) {
       return Fn + (size_t)(k < nin ? ib + k : I.out_idx[ob + k - nin]) * I.ld;
     };
-    // four edge rows in flight, summed in edge order (the same order as one at a time)
-    int k = 0;
-    for (; k + 4 <= deg; k += 4) {
-      const float* r[4] = {row(k), row(k + 1), row(k + 2), row(k + 3)};
-#pragma unroll
-      for (int v = 0; v < VPT; ++v) {
-        const int ci = v * GROUP + lane;
-        if (ci < nchunks) {
-          P fr[4][VW];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) ld_plain<P, VW>(r[q] + ci * VW, fr[q]);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const P sg = k + q < nin ? P(1) : P(-1);
-#pragma unroll
-            for (int u = 0; u < VW; ++u) s[v][u] += sg * fr[q][u];
-          }
-        }
-      }
-    }
-    for (; k < deg; ++k) {
-      const float* r = row(k);
-      const P sg = k < nin ? P(1) : P(-1);
-#pragma unroll
-      for (int v = 0; v < VPT; ++v) {
-        const int ci = v * GROUP + lane;
-        if (ci < nchunks) {
-          P fr[VW];
-          ld_plain<P, VW>(r + ci * VW, fr);
-#pragma unroll
-          for (int u = 0; u < VW; ++u) s[v][u] += sg * fr[u];
-        }
-      }
-    }
     P loc[NODE_PARTS];
 #pragma unroll
     for (int kk = 0; kk < NODE_PARTS; ++kk) loc[kk] = P(0);
@@ -258,10 +219,34 @@ batch_node_kernel(const BatchInst* __restrict__ insts, BatchClassDev cls) {
     const float* yrow = I.Y[par] + (size_t)j * I.ld;
     const float* wrow = I.W + (size_t)j * I.ld;
     const float* grow = I.Gm ? I.Gm + (size_t)j * I.ld : nullptr;
-#pragma unroll
+    // one 4-entry chunk at a time (only its accumulator is live): the chunk's sum over the
+    // node's edge rows, four rows in flight and added in edge order, then its dual update
+#pragma unroll 1
     for (int v = 0; v < VPT; ++v) {
       const int ci = v * GROUP + lane;
       if (ci >= nchunks) continue;
+      P sv[VW];
+#pragma unroll
+      for (int u = 0; u < VW; ++u) sv[u] = P(0);
+      int k = 0;
+      for (; k + 4 <= deg; k += 4) {
+        P fr[4][VW];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ld_plain<P, VW>(row(k + q) + ci * VW, fr[q]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const P sg = k + q < nin ? P(1) : P(-1);
+#pragma unroll
+          for (int u = 0; u < VW; ++u) sv[u] += sg * fr[q][u];
+        }
+      }
+      for (; k < deg; ++k) {
+        P fr[VW];
+        ld_plain<P, VW>(row(k) + ci * VW, fr);
+        const P sg = k < nin ? P(1) : P(-1);
+#pragma unroll
+        for (int u = 0; u < VW; ++u) sv[u] += sg * fr[u];
+      }
       P po[VW], yo[VW], wv[VW], gv[VW], yn[VW], that_v[VW], up_v[VW], yh_v[VW], yl[VW];
       ld_plain<P, VW>(prow + ci * VW, po);
       ld_plain<P, VW>(yrow + ci * VW, yo);
@@ -277,7 +262,7 @@ batch_node_kernel(const BatchInst* __restrict__ insts, BatchClassDev cls) {
 #pragma unroll
       for (int u = 0; u < VW; ++u) {
         const int i = ci * VW + u;
-        const P fhat_at = (s[v][u] - (P(1) - rho) * po[u]) * inv_rho;
+        const P fhat_at = (sv[u] - (P(1) - rho) * po[u]) * inv_rho;
         const P fplus_at = P(2) * fhat_at - po[u];
         const bool live = (i < I.n) && (i != j);
         P delta, tr = P(0);
@@ -317,7 +302,7 @@ batch_node_kernel(const BatchInst* __restrict__ insts, BatchClassDev cls) {
       }
       if (I.Ylo[par ^ 1]) st_lo<VW>(I.Ylo[par ^ 1] + (size_t)j * I.ld + ci * VW, yl);
       st_plain<P, VW>(I.Y[par ^ 1] + (size_t)j * I.ld + ci * VW, yn);
-      st_plain<P, VW>(prow + ci * VW, s[v]);
+      st_plain<P, VW>(prow + ci * VW, sv);
       if (check) {
         st_plain<P, VW>(I.That + (size_t)j * I.ld + ci * VW, that_v);
         st_plain<P, VW>(I.Uprime + (size_t)j * I.ld + ci * VW, up_v);

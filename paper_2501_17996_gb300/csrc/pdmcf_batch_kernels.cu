@@ -7,7 +7,9 @@ template <int IDX>
 static void fill_batch(BatchTable& t) {
   constexpr ShapeDesc d = kShapes[IDX];
   constexpr int MB = min_blocks<float, d.vpt, 4, d.block>();
-  constexpr int MBN = min_blocks_batch_node<float, d.vpt, 4, d.block>();
+  // the node phase works one chunk at a time (its registers do not grow with vpt): 1024
+  // threads per SM
+  constexpr int MBN = 1024 / d.block > 0 ? 1024 / d.block : 1;
   t.edge[IDX] = batch_edge_kernel<d.vpt, d.group, d.block, MB>;
   t.node[IDX] = batch_node_kernel<d.vpt, d.group, d.block, MBN>;
   t.check[IDX] = batch_check_kernel<d.vpt, d.group, d.block, MB>;

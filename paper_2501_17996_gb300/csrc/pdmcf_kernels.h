@@ -76,14 +76,6 @@ constexpr int min_blocks_node() {
   return 1024 / BLOCK > 0 ? 1024 / BLOCK : 1;
 }
 
-// The batched node phase keeps every chunk's accumulator live: half the residency once they
-// exceed 48 bytes per thread.
-template <typename P, int VPT, int VW, int BLOCK>
-constexpr int min_blocks_batch_node() {
-  return (VPT * VW * (int)sizeof(P) <= 48) ? (1024 / BLOCK > 0 ? 1024 / BLOCK : 1)
-                                           : (512 / BLOCK > 0 ? 512 / BLOCK : 1);
-}
-
 namespace pdmcf {
 template <typename P, typename S, int IDX>
 void fill_shape(KernelTable<P, S>& t) {
