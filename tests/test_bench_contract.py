@@ -100,3 +100,19 @@ def test_oracle_with_the_parallel_step_matches_the_oracle():
     assert np.abs(T - ref.T).max() <= 1e-9 * np.abs(ref.T).max()
     assert abs(U - ref.utility) <= 1e-11 * abs(ref.utility)
     assert abs(om - ref.omega) <= 1e-9 * ref.omega
+
+
+def test_committed_traffic_captures_match_the_kernel_sources():
+    """The DRAM bytes the bench reports as `roofline.traffic` come from the committed one-pass
+    captures; each names the hash of the kernel sources it was taken on, and the bench uses it
+    only while the hash matches. The committed captures are those of the current kernels."""
+    bench = _bench_module()
+    h = bench.kernel_source_hash()
+    prof = os.path.join(ROOT, "profiles")
+    caps = [f for f in os.listdir(prof) if f.startswith("edge_kernel_large_") and f.endswith(".json")]
+    assert caps
+    for f in caps:
+        d = json.load(open(os.path.join(prof, f)))
+        assert d["kernel_source_hash"] == h, f
+        assert d["dram_bytes_per_launch"] == d["dram_bytes_read"] + d["dram_bytes_write"], f
+        assert "--clock-control none" in d["command"], f
